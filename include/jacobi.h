@@ -1,0 +1,214 @@
+/*
+ * jacobi.h -- C ABI of libjac, a GB300 (sm_103a) library for the 3-D
+ * 19-point variable-coefficient Jacobi relaxation with a fused residual.
+ *
+ * The operation.  The paper (Yamato, "Improvement of Automatic GPU Offloading
+ * Technology for Application Loop Statements") offloads the loop nests of
+ * C/C++ applications, evaluated on the Himeno benchmark, a Poisson solve by
+ * Jacobi iteration (Section 5.1.1).  One sweep, for every interior point
+ * x = (i, j, k) (1 <= i <= I-2, same for j and k), reading state p and writing
+ * state p':
+ *
+ *   s0 = a0 p[i+1] + a1 p[j+1] + a2 p[k+1]
+ *      + b0 (p[i+1,j+1] - p[i+1,j-1] - p[i-1,j+1] + p[i-1,j-1])
+ *      + b1 (p[j+1,k+1] - p[j+1,k-1] - p[j-1,k+1] + p[j-1,k-1])
+ *      + b2 (p[i+1,k+1] - p[i+1,k-1] - p[i-1,k+1] + p[i-1,k-1])
+ *      + c0 p[i-1] + c1 p[j-1] + c2 p[k-1] + wrk1
+ *   ss = (s0 a3 - p[x]) bnd
+ *   p'[x] = p[x] + omega ss
+ *
+ * with every coefficient read at x.  Faces are never written.  The residual
+ * of a sweep is gosa = sum over the interior of ss^2, taken from that sweep's
+ * input state.  The paper's transfer hoisting (Section 3.2-3.3: copy data
+ * once, outside the outermost loop, and mark it present on the device
+ * afterwards) is the structure of this API: jac_upload once, jac_sweep n
+ * times with every array resident in device memory, jac_download once.
+ *
+ * Conventions.
+ *   - Every call returns a jac_status.  No call aborts or prints;
+ *     jac_last_error() gives the message of the last failure of a context.
+ *   - Host arrays ("host fields") are dense FP64, i fastest, then j, then k:
+ *     element (i, j, k) at index (k*J + j)*I + i.
+ *   - Device storage ("storage layout") is pitched: element (i, j, k) of an
+ *     array at offset (k*J + j)*pitch + i elements, pitch = jac_pitch(I).
+ *     Element types by precision:
+ *       JAC_F64:          every array double;
+ *       JAC_F32:          every array float;
+ *       JAC_F32_BF16COEF: p and wrk1 float, the eleven coefficient arrays
+ *                         a0..a3, b0..b2, c0..c2 and bnd __nv_bfloat16.
+ *     Storage values are RNE roundings of the FP64 inputs (BF16 values are
+ *     RNE of the FP32-rounded value).  Arithmetic is in the element type of
+ *     p; residuals are accumulated in FP64.
+ *   - Calls that take a stream enqueue asynchronously on it unless they
+ *     return host data, in which case they synchronise that stream.
+ *   - The library never calls exit or abort, and device-side waits are
+ *     bounded: a wait that runs out sets an error word that the next
+ *     synchronising call reports as JAC_ETIMEOUT.
+ */
+#ifndef JACOBI_H
+#define JACOBI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum jac_status {
+    JAC_OK = 0,
+    JAC_EINVAL = 1,    /* bad argument: size, pointer, alignment, precision */
+    JAC_ENOMEM = 2,    /* a device or host allocation failed */
+    JAC_ECUDA = 3,     /* a CUDA runtime or driver call failed */
+    JAC_ESTATE = 4,    /* call not valid in the current state */
+    JAC_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
+    JAC_EINTERNAL = 6  /* an internal consistency check failed */
+} jac_status;
+
+typedef enum jac_prec {
+    JAC_F64 = 0,          /* FP64 storage and arithmetic */
+    JAC_F32 = 1,          /* FP32 storage and arithmetic */
+    JAC_F32_BF16COEF = 2  /* FP32 p/wrk1 and arithmetic, BF16 coefficients */
+} jac_prec;
+
+/* Array indices of a field set. */
+enum {
+    JAC_P = 0, JAC_A0, JAC_A1, JAC_A2, JAC_A3, JAC_B0, JAC_B1, JAC_B2,
+    JAC_C0, JAC_C1, JAC_C2, JAC_WRK1, JAC_BND, JAC_NFIELDS
+};
+
+/* Thirteen dense FP64 arrays (host or device memory, as the call says),
+ * indexed by the enum above.  Borrowed for the duration of the call. */
+typedef struct jac_fields {
+    const double *f[JAC_NFIELDS];
+} jac_fields;
+
+/* Storage pitch (elements) of every array of an I-wide grid: I rounded up to
+ * a multiple of 8, so that each row starts on a 16-byte boundary in every
+ * element type (the TMA stride rule) and vector loads stay aligned. */
+int jac_pitch(int I);
+
+/* Library version string (static storage). */
+const char *jac_version(void);
+
+/* =====================================================================
+ * Stateless device API.  The caller owns every buffer.
+ * ===================================================================== */
+
+/* One grid in storage layout.  p[0] and p[1] are the two state buffers:
+ * sweep t (t = 0, 1, ...) of a call reads p[t % 2] and writes p[(t+1) % 2],
+ * so after n sweeps the state is in p[n % 2].  Faces (and the padding
+ * columns I..pitch-1) of both buffers must hold the same values; sweeps never
+ * write faces.  coef[q] for q = JAC_A0..JAC_BND (q = 1..12, JAC_WRK1
+ * included) points at that array; coef[0] is unused.  Every pointer must be
+ * 16-byte aligned. */
+typedef struct jac_grid {
+    int I, J, K;          /* >= 3 each */
+    jac_prec prec;
+    double omega;
+    void *p[2];
+    const void *coef[JAC_NFIELDS];
+} jac_grid;
+
+/* Launch shape of the sweep kernel: rows per CTA (tile_j, one warp per
+ * row of 32 vectors) and k-planes per CTA (kdepth).  {0, 0} picks defaults. */
+typedef struct jac_plan {
+    int tile_j;   /* 4, 8 or 16 */
+    int kdepth;   /* >= 1 */
+} jac_plan;
+
+/* Bytes of device workspace jac_sweep_dev needs for this grid and plan. */
+jac_status jac_sweep_workspace_size(const jac_grid *g, const jac_plan *plan, size_t *bytes);
+
+/* n_iter sweeps of grid g on the given stream (a cudaStream_t, NULL for the
+ * legacy default stream).  If d_residual is not NULL, the residual of the
+ * last sweep is written there (one double, device memory).  workspace: device
+ * memory of at least jac_sweep_workspace_size bytes, 16-byte aligned; its
+ * first 256 bytes must be zero before the first call that uses it (the
+ * kernels leave them zero again).  Calls that share a workspace must not
+ * overlap in time.  n_iter == 0 is a no-op.  Errors: JAC_EINVAL for a bad
+ * grid, plan or size; JAC_ECUDA if a launch fails. */
+jac_status jac_sweep_dev(const jac_grid *g, const jac_plan *plan, int n_iter,
+                         double *d_residual, void *workspace, size_t ws_bytes,
+                         void *stream);
+
+/* Reads the device error word kept in a workspace (synchronises the
+ * stream): JAC_OK, or JAC_ETIMEOUT if a bounded wait gave up; clears it. */
+jac_status jac_workspace_check(void *workspace, void *stream);
+
+/* Convert one dense FP64 device array (I*J*K doubles) into storage layout of
+ * element type `prec` uses for array `which` (JAC_P .. JAC_BND), on stream.
+ * Padding columns are set to zero. */
+jac_status jac_pack_dev(int I, int J, int K, jac_prec prec, int which,
+                        const double *d_src, void *d_dst, void *stream);
+
+/* Convert one storage-layout array back to dense FP64 (device memory). */
+jac_status jac_unpack_dev(int I, int J, int K, jac_prec prec, int which,
+                          const void *d_src, double *d_dst, void *stream);
+
+/* =====================================================================
+ * Context API: one grid, resident in device memory owned by the context.
+ * ===================================================================== */
+typedef struct jac_ctx jac_ctx;
+
+/* Create a context for an I x J x K grid.  Allocates the storage of all
+ * fields, both state buffers, a FP64 staging array of I*J*K doubles and the
+ * sweep workspace (cudaMalloc on the current device).  stream: the
+ * cudaStream_t every call of this context uses (NULL: legacy default).
+ * Errors: JAC_EINVAL (dims < 3, bad precision, omega not finite),
+ * JAC_ENOMEM, JAC_ECUDA. */
+jac_status jac_create(jac_ctx **out, int I, int J, int K, jac_prec prec,
+                      double omega, void *stream);
+
+/* Free everything the context owns (synchronises its stream).  NULL is ok. */
+jac_status jac_destroy(jac_ctx *ctx);
+
+/* Message of the last failed call on this context ("" if none). */
+const char *jac_last_error(const jac_ctx *ctx);
+
+/* Set the launch plan of later sweeps ({0,0} = defaults). */
+jac_status jac_set_plan(jac_ctx *ctx, const jac_plan *plan);
+
+/* The hoisted copy-in: all thirteen host FP64 arrays, rounded to the storage
+ * precision on the device; p0 goes to both state buffers.  Resets the sweep
+ * count and the residual.  Returns after the copies are enqueued (host
+ * arrays may be reused once the call returns: pageable sources are copied
+ * synchronously, and the call synchronises before returning). */
+jac_status jac_upload(jac_ctx *ctx, const jac_fields *host);
+
+/* Same as jac_upload with the thirteen arrays in device memory (dense FP64);
+ * asynchronous. */
+jac_status jac_upload_dev(jac_ctx *ctx, const jac_fields *dev);
+
+/* n_iter sweeps, asynchronous; the residual of the last one is kept on the
+ * device.  JAC_ESTATE before the first upload. */
+jac_status jac_sweep(jac_ctx *ctx, int n_iter);
+
+/* Residual of the last sweep (synchronises).  JAC_ESTATE if no sweep ran
+ * since the last upload; JAC_ETIMEOUT if a device wait gave up. */
+jac_status jac_residual(jac_ctx *ctx, double *out);
+
+/* The hoisted copy-out: current state as dense FP64 into host memory
+ * (I*J*K doubles; synchronises). */
+jac_status jac_download(jac_ctx *ctx, double *p_host);
+
+/* Current state as dense FP64 into device memory (asynchronous). */
+jac_status jac_download_dev(jac_ctx *ctx, double *p_dev);
+
+/* Sweeps completed since the last upload. */
+jac_status jac_sweep_count(const jac_ctx *ctx, long long *out);
+
+/* The context's grid descriptor (current state in p[count % 2] order is
+ * handled by the context; g->p[0] is the current state after this call). */
+jac_status jac_get_grid(const jac_ctx *ctx, jac_grid *g);
+
+/* The contrast to hoisting, for measurement only: for each of n_iter
+ * sweeps, copy all thirteen host arrays in (the current host state as p),
+ * run one sweep, copy p back out to p_host.  On entry p_host holds p0; on
+ * return it holds p_n, and the context's residual is that of sweep n. */
+jac_status jac_sweep_unhoisted(jac_ctx *ctx, int n_iter, const jac_fields *host,
+                               double *p_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JACOBI_H */

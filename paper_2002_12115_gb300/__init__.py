@@ -1,0 +1,19 @@
+"""GB300-native 19-point variable-coefficient Jacobi relaxation (libjac).
+
+The hot path of the loop-nest applications that Yamato's automatic GPU
+offloading targets (the Himeno benchmark of Section 5.1.1): a device-resident
+3-D 19-point Jacobi sweep with a fused residual, behind the C ABI in
+include/jacobi.h, with hand-written sm_103a CUDA kernels.
+
+    from paper_2002_12115_gb300 import Jacobi
+    with Jacobi(I, J, K, prec="f32") as jac:
+        jac.upload(fields)        # one copy-in
+        jac.sweep(1000)           # resident sweeps
+        gosa = jac.residual()     # residual of the last sweep
+        p = jac.download()        # one copy-out
+"""
+from .binding import (FIELDS, PRECS, JacError, Jacobi, check, jac_fields, jac_grid, jac_plan, lib, pitch,
+                      stream_handle, sweep_dev, workspace_size)
+
+__all__ = ["FIELDS", "PRECS", "JacError", "Jacobi", "check", "jac_fields", "jac_grid", "jac_plan", "lib",
+           "pitch", "stream_handle", "sweep_dev", "workspace_size"]

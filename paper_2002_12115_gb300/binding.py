@@ -1,0 +1,242 @@
+"""ctypes binding of libjac (include/jacobi.h): argument marshalling only.
+
+Every step of the sweep runs in the CUDA library; this module converts
+numpy arrays / torch tensors to pointers and status codes to exceptions.
+If libjac.so has not been built, loading raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libjac.so")
+
+# status codes
+JAC_OK, JAC_EINVAL, JAC_ENOMEM, JAC_ECUDA, JAC_ESTATE, JAC_ETIMEOUT, JAC_EINTERNAL = range(7)
+STATUS_NAMES = {0: "JAC_OK", 1: "JAC_EINVAL", 2: "JAC_ENOMEM", 3: "JAC_ECUDA", 4: "JAC_ESTATE",
+                5: "JAC_ETIMEOUT", 6: "JAC_EINTERNAL"}
+# precisions
+PRECS = {"f64": 0, "f32": 1, "bf16": 2}
+# array indices of a field set
+FIELDS = ("p", "a0", "a1", "a2", "a3", "b0", "b1", "b2", "c0", "c1", "c2", "wrk1", "bnd")
+NFIELDS = len(FIELDS)
+
+
+class JacError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class jac_fields(ctypes.Structure):
+    _fields_ = [("f", ctypes.c_void_p * NFIELDS)]
+
+
+class jac_grid(ctypes.Structure):
+    _fields_ = [("I", ctypes.c_int), ("J", ctypes.c_int), ("K", ctypes.c_int), ("prec", ctypes.c_int),
+                ("omega", ctypes.c_double), ("p", ctypes.c_void_p * 2),
+                ("coef", ctypes.c_void_p * NFIELDS)]
+
+
+class jac_plan(ctypes.Structure):
+    _fields_ = [("tile_j", ctypes.c_int), ("kdepth", ctypes.c_int)]
+
+
+_VP = ctypes.c_void_p
+_I = ctypes.c_int
+_SIG = {
+    "jac_pitch": (_I, [_I]),
+    "jac_version": (ctypes.c_char_p, []),
+    "jac_sweep_workspace_size": (_I, [ctypes.POINTER(jac_grid), ctypes.POINTER(jac_plan),
+                                      ctypes.POINTER(ctypes.c_size_t)]),
+    "jac_sweep_dev": (_I, [ctypes.POINTER(jac_grid), ctypes.POINTER(jac_plan), _I, _VP, _VP,
+                           ctypes.c_size_t, _VP]),
+    "jac_workspace_check": (_I, [_VP, _VP]),
+    "jac_pack_dev": (_I, [_I, _I, _I, _I, _I, _VP, _VP, _VP]),
+    "jac_unpack_dev": (_I, [_I, _I, _I, _I, _I, _VP, _VP, _VP]),
+    "jac_create": (_I, [ctypes.POINTER(_VP), _I, _I, _I, _I, ctypes.c_double, _VP]),
+    "jac_destroy": (_I, [_VP]),
+    "jac_last_error": (ctypes.c_char_p, [_VP]),
+    "jac_set_plan": (_I, [_VP, ctypes.POINTER(jac_plan)]),
+    "jac_upload": (_I, [_VP, ctypes.POINTER(jac_fields)]),
+    "jac_upload_dev": (_I, [_VP, ctypes.POINTER(jac_fields)]),
+    "jac_sweep": (_I, [_VP, _I]),
+    "jac_residual": (_I, [_VP, ctypes.POINTER(ctypes.c_double)]),
+    "jac_download": (_I, [_VP, _VP]),
+    "jac_download_dev": (_I, [_VP, _VP]),
+    "jac_sweep_count": (_I, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
+    "jac_get_grid": (_I, [_VP, ctypes.POINTER(jac_grid)]),
+    "jac_sweep_unhoisted": (_I, [_VP, _I, ctypes.POINTER(jac_fields), _VP]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libjac; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"libjac.so not built ({LIB_PATH}); run __graft_entry__.build() "
+                                  "or python -m paper_2002_12115_gb300._build")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIG.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def check(status: int, ctx=None) -> None:
+    if status != JAC_OK:
+        msg = lib().jac_last_error(ctx)
+        raise JacError(status, msg.decode() if msg else "")
+
+
+def stream_handle(stream=None) -> int:
+    """cudaStream_t of a torch stream (default: the current stream)."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def pitch(I: int) -> int:
+    return int(lib().jac_pitch(int(I)))
+
+
+def _host_ptr(a: np.ndarray) -> int:
+    if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("host fields must be C-contiguous float64 arrays")
+    return a.ctypes.data
+
+
+class Jacobi:
+    """One grid resident on the GPU (a jac_ctx).
+
+    ``upload`` -> ``sweep(n)`` -> ``residual()`` / ``download()`` is the
+    hoisted structure: one copy-in, n sweeps on resident arrays, one copy-out.
+    Arrays are (K, J, I) float64, i fastest.
+    """
+
+    def __init__(self, I: int, J: int, K: int, prec: str = "f32", omega: float = 0.8, stream=None):
+        import torch
+        if prec not in PRECS:
+            raise ValueError(f"prec must be one of {list(PRECS)}")
+        self.I, self.J, self.K, self.prec, self.omega = int(I), int(J), int(K), prec, float(omega)
+        self._stream_obj = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = stream_handle(self._stream_obj)
+        h = _VP()
+        check(lib().jac_create(ctypes.byref(h), self.I, self.J, self.K, PRECS[prec], self.omega,
+                               _VP(self.stream)))
+        self._h = h
+
+    # -- lifetime
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().jac_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def shape(self):
+        return (self.K, self.J, self.I)
+
+    def _check(self, st: int) -> None:
+        check(st, self._h)
+
+    def _fields(self, arrays: dict, device: bool) -> jac_fields:
+        f = jac_fields()
+        for q, name in enumerate(FIELDS):
+            a = arrays[name]
+            if device:
+                if tuple(a.shape) != self.shape or a.dtype.__str__() != "torch.float64" or not a.is_contiguous():
+                    raise ValueError(f"{name}: expected a contiguous float64 CUDA tensor of shape {self.shape}")
+                f.f[q] = a.data_ptr()
+            else:
+                if tuple(a.shape) != self.shape:
+                    raise ValueError(f"{name}: expected shape {self.shape}")
+                f.f[q] = _host_ptr(a)
+        return f
+
+    # -- the hoisted path
+    def set_plan(self, tile_j: int = 0, kdepth: int = 0) -> None:
+        self._check(lib().jac_set_plan(self._h, ctypes.byref(jac_plan(int(tile_j), int(kdepth)))))
+
+    def upload(self, fields: dict) -> None:
+        """Copy in all thirteen host arrays (float64, shape (K, J, I))."""
+        f = self._fields(fields, device=False)
+        self._check(lib().jac_upload(self._h, ctypes.byref(f)))
+
+    def upload_tensors(self, fields: dict) -> None:
+        """Same, from contiguous float64 CUDA tensors."""
+        f = self._fields(fields, device=True)
+        self._check(lib().jac_upload_dev(self._h, ctypes.byref(f)))
+
+    def sweep(self, n: int) -> None:
+        self._check(lib().jac_sweep(self._h, int(n)))
+
+    def residual(self) -> float:
+        out = ctypes.c_double()
+        self._check(lib().jac_residual(self._h, ctypes.byref(out)))
+        return out.value
+
+    def download(self, out: np.ndarray | None = None) -> np.ndarray:
+        if out is None:
+            out = np.empty(self.shape, dtype=np.float64)
+        self._check(lib().jac_download(self._h, _VP(_host_ptr(out))))
+        return out
+
+    def download_tensor(self, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        self._check(lib().jac_download_dev(self._h, _VP(out.data_ptr())))
+        return out
+
+    def count(self) -> int:
+        c = ctypes.c_longlong()
+        self._check(lib().jac_sweep_count(self._h, ctypes.byref(c)))
+        return c.value
+
+    def grid(self) -> jac_grid:
+        g = jac_grid()
+        self._check(lib().jac_get_grid(self._h, ctypes.byref(g)))
+        return g
+
+    def sweep_unhoisted(self, n: int, fields: dict, p_host: np.ndarray) -> None:
+        """Per-sweep copy-in / copy-out (measurement contrast only)."""
+        f = self._fields(fields, device=False)
+        self._check(lib().jac_sweep_unhoisted(self._h, int(n), ctypes.byref(f), _VP(_host_ptr(p_host))))
+
+
+def workspace_size(grid: jac_grid, tile_j: int = 0, kdepth: int = 0) -> int:
+    n = ctypes.c_size_t()
+    check(lib().jac_sweep_workspace_size(ctypes.byref(grid), ctypes.byref(jac_plan(tile_j, kdepth)),
+                                         ctypes.byref(n)))
+    return n.value
+
+
+def sweep_dev(grid: jac_grid, n: int, d_residual: int | None, workspace: int, ws_bytes: int,
+              stream: int, tile_j: int = 0, kdepth: int = 0) -> None:
+    """The stateless entry point jac_sweep_dev on caller-owned device buffers."""
+    check(lib().jac_sweep_dev(ctypes.byref(grid), ctypes.byref(jac_plan(tile_j, kdepth)), int(n),
+                              _VP(d_residual) if d_residual else None, _VP(workspace), ctypes.c_size_t(ws_bytes),
+                              _VP(stream)))

@@ -1,0 +1,292 @@
+// Context API of libjac: one grid resident in device memory owned by the
+// context.  jac_upload is the hoisted copy-in, jac_sweep runs every sweep on
+// the resident arrays, jac_download is the hoisted copy-out -- the transfer
+// structure the paper builds its offloading on (Sections 3.2-3.3: transfer
+// nested-loop variables once, outside the outermost loop, batch the copies
+// and mark data already present on the device).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "jac_common.cuh"
+#include "jac_internal.h"
+
+struct jac_ctx {
+    int I = 0, J = 0, K = 0, pitch = 0;
+    jac_prec prec = JAC_F32;
+    double omega = 0.0;
+    cudaStream_t stream = nullptr;
+    void *arena = nullptr;            // field storage: both states and 12 arrays
+    void *arr[JAC_NFIELDS] = {};      // arr[JAC_A0..JAC_BND]; arr[JAC_P] unused
+    void *pbuf[2] = {nullptr, nullptr};
+    int cur = 0;                      // which pbuf holds the current state
+    double *staging = nullptr;        // I*J*K doubles
+    void *ws = nullptr;               // sweep workspace
+    size_t ws_bytes = 0;
+    jac_plan plan{0, 0};
+    long long count = 0;
+    bool uploaded = false;
+    bool has_res = false;
+    std::string err;
+};
+
+namespace {
+
+jac_status ctx_fail(jac_ctx *c, jac_status s, const std::string &m)
+{
+    if (c) c->err = m;
+    jac::set_thread_error(m);
+    return s;
+}
+
+jac_status ctx_from_thread(jac_ctx *c, jac_status s)
+{
+    if (s != JAC_OK && c) c->err = jac::thread_last_error();
+    return s;
+}
+
+jac_status ctx_cuda(jac_ctx *c, cudaError_t e, const char *what)
+{
+    return ctx_fail(c, JAC_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+size_t array_bytes(const jac_ctx *c, int which)
+{
+    return jac::round_up((size_t)c->pitch * c->J * c->K * jac::elem_bytes(c->prec, which), 256);
+}
+
+jac_grid make_grid(const jac_ctx *c)
+{
+    jac_grid g;
+    std::memset(&g, 0, sizeof(g));
+    g.I = c->I; g.J = c->J; g.K = c->K;
+    g.prec = c->prec;
+    g.omega = c->omega;
+    g.p[0] = c->pbuf[c->cur];
+    g.p[1] = c->pbuf[c->cur ^ 1];
+    for (int q = JAC_A0; q <= JAC_BND; ++q) g.coef[q] = c->arr[q];
+    return g;
+}
+
+jac_status ensure_workspace(jac_ctx *c)
+{
+    jac_grid g = make_grid(c);
+    size_t need = 0;
+    jac_status s = jac_sweep_workspace_size(&g, &c->plan, &need);
+    if (s != JAC_OK) return ctx_from_thread(c, s);
+    if (need <= c->ws_bytes) return JAC_OK;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return ctx_cuda(c, e, "cudaStreamSynchronize");
+    if (c->ws) cudaFree(c->ws);
+    c->ws = nullptr;
+    c->ws_bytes = 0;
+    e = cudaMalloc(&c->ws, need);
+    if (e != cudaSuccess) return ctx_fail(c, JAC_ENOMEM, "workspace allocation failed");
+    e = cudaMemsetAsync(c->ws, 0, need, c->stream);
+    if (e != cudaSuccess) return ctx_cuda(c, e, "cudaMemsetAsync");
+    c->ws_bytes = need;
+    return JAC_OK;
+}
+
+jac_status upload_impl(jac_ctx *c, const jac_fields *f, bool on_device)
+{
+    if (!c) return ctx_fail(c, JAC_EINVAL, "ctx is NULL");
+    if (!f) return ctx_fail(c, JAC_EINVAL, "fields is NULL");
+    for (int q = 0; q < JAC_NFIELDS; ++q)
+        if (!f->f[q]) return ctx_fail(c, JAC_EINVAL, "field " + std::to_string(q) + " is NULL");
+    const size_t n = (size_t)c->I * c->J * c->K;
+    for (int q = 0; q < JAC_NFIELDS; ++q) {
+        const double *src = f->f[q];
+        if (!on_device) {
+            cudaError_t e = cudaMemcpyAsync(c->staging, src, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+            if (e != cudaSuccess) return ctx_cuda(c, e, "host-to-device copy");
+            src = c->staging;
+        }
+        void *dst = (q == JAC_P) ? c->pbuf[0] : c->arr[q];
+        jac_status s = jac::pack_dev(c->I, c->J, c->K, c->prec, q, src, dst, c->stream);
+        if (s != JAC_OK) return ctx_from_thread(c, s);
+    }
+    cudaError_t e = cudaMemcpyAsync(c->pbuf[1], c->pbuf[0], array_bytes(c, JAC_P), cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return ctx_cuda(c, e, "device copy of p0");
+    if (!on_device) {
+        e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return ctx_cuda(c, e, "cudaStreamSynchronize");
+    }
+    c->cur = 0;
+    c->count = 0;
+    c->uploaded = true;
+    c->has_res = false;
+    return JAC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+jac_status jac_create(jac_ctx **out, int I, int J, int K, jac_prec prec, double omega, void *stream)
+{
+    if (!out) return ctx_fail(nullptr, JAC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (I < 3 || J < 3 || K < 3) return ctx_fail(nullptr, JAC_EINVAL, "every grid dimension must be >= 3");
+    if (prec != JAC_F64 && prec != JAC_F32 && prec != JAC_F32_BF16COEF)
+        return ctx_fail(nullptr, JAC_EINVAL, "unknown precision");
+    if (!std::isfinite(omega)) return ctx_fail(nullptr, JAC_EINVAL, "omega must be finite");
+    jac_ctx *c = new (std::nothrow) jac_ctx;
+    if (!c) return ctx_fail(nullptr, JAC_ENOMEM, "host allocation failed");
+    c->I = I; c->J = J; c->K = K;
+    c->pitch = jac_pitch(I);
+    c->prec = prec;
+    c->omega = omega;
+    c->stream = static_cast<cudaStream_t>(stream);
+    size_t total = 2 * array_bytes(c, JAC_P);
+    for (int q = JAC_A0; q <= JAC_BND; ++q) total += array_bytes(c, q);
+    cudaError_t e = cudaMalloc(&c->arena, total);
+    if (e != cudaSuccess) {
+        delete c;
+        return ctx_fail(nullptr, JAC_ENOMEM, "device allocation of the fields failed");
+    }
+    char *p = static_cast<char *>(c->arena);
+    c->pbuf[0] = p; p += array_bytes(c, JAC_P);
+    c->pbuf[1] = p; p += array_bytes(c, JAC_P);
+    for (int q = JAC_A0; q <= JAC_BND; ++q) {
+        c->arr[q] = p;
+        p += array_bytes(c, q);
+    }
+    e = cudaMalloc(reinterpret_cast<void **>(&c->staging), (size_t)I * J * K * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaFree(c->arena);
+        delete c;
+        return ctx_fail(nullptr, JAC_ENOMEM, "device allocation of the staging array failed");
+    }
+    e = cudaMemsetAsync(c->arena, 0, total, c->stream);
+    if (e != cudaSuccess) {
+        jac_status s = ctx_cuda(nullptr, e, "cudaMemsetAsync");
+        cudaFree(c->staging);
+        cudaFree(c->arena);
+        delete c;
+        return s;
+    }
+    jac_status s = ensure_workspace(c);
+    if (s != JAC_OK) {
+        cudaFree(c->staging);
+        cudaFree(c->arena);
+        delete c;
+        return s;
+    }
+    *out = c;
+    return JAC_OK;
+}
+
+jac_status jac_destroy(jac_ctx *c)
+{
+    if (!c) return JAC_OK;
+    cudaStreamSynchronize(c->stream);
+    if (c->ws) cudaFree(c->ws);
+    if (c->staging) cudaFree(c->staging);
+    if (c->arena) cudaFree(c->arena);
+    delete c;
+    return JAC_OK;
+}
+
+const char *jac_last_error(const jac_ctx *c) { return c ? c->err.c_str() : jac::thread_last_error(); }
+
+jac_status jac_set_plan(jac_ctx *c, const jac_plan *plan)
+{
+    if (!c) return ctx_fail(c, JAC_EINVAL, "ctx is NULL");
+    jac_plan p{0, 0};
+    if (plan) p = *plan;
+    if (p.tile_j != 0 && p.tile_j != 4 && p.tile_j != 8 && p.tile_j != 16)
+        return ctx_fail(c, JAC_EINVAL, "tile_j must be 0, 4, 8 or 16");
+    if (p.kdepth < 0) return ctx_fail(c, JAC_EINVAL, "kdepth must be >= 0");
+    c->plan = p;
+    return ensure_workspace(c);
+}
+
+jac_status jac_upload(jac_ctx *c, const jac_fields *host) { return upload_impl(c, host, false); }
+
+jac_status jac_upload_dev(jac_ctx *c, const jac_fields *dev) { return upload_impl(c, dev, true); }
+
+jac_status jac_sweep(jac_ctx *c, int n_iter)
+{
+    if (!c) return ctx_fail(c, JAC_EINVAL, "ctx is NULL");
+    if (!c->uploaded) return ctx_fail(c, JAC_ESTATE, "jac_sweep before jac_upload");
+    if (n_iter < 0) return ctx_fail(c, JAC_EINVAL, "n_iter must be >= 0");
+    if (n_iter == 0) return JAC_OK;
+    jac_status s = ensure_workspace(c);
+    if (s != JAC_OK) return s;
+    jac_grid g = make_grid(c);
+    jac::WsHeader *hdr = static_cast<jac::WsHeader *>(c->ws);
+    s = jac::sweep_dev(&g, &c->plan, n_iter, &hdr->residual, c->ws, c->ws_bytes, c->stream);
+    if (s != JAC_OK) return ctx_from_thread(c, s);
+    c->cur = (c->cur + n_iter) & 1;
+    c->count += n_iter;
+    c->has_res = true;
+    return JAC_OK;
+}
+
+jac_status jac_residual(jac_ctx *c, double *out)
+{
+    if (!c || !out) return ctx_fail(c, JAC_EINVAL, "NULL argument");
+    if (!c->has_res) return ctx_fail(c, JAC_ESTATE, "no sweep since the last upload");
+    jac_status s = jac::workspace_check(c->ws, c->stream);
+    if (s != JAC_OK) return ctx_from_thread(c, s);
+    jac::WsHeader *hdr = static_cast<jac::WsHeader *>(c->ws);
+    cudaError_t e = cudaMemcpyAsync(out, &hdr->residual, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return ctx_cuda(c, e, "residual copy");
+    return JAC_OK;
+}
+
+jac_status jac_download_dev(jac_ctx *c, double *p_dev)
+{
+    if (!c || !p_dev) return ctx_fail(c, JAC_EINVAL, "NULL argument");
+    if (!c->uploaded) return ctx_fail(c, JAC_ESTATE, "download before upload");
+    return ctx_from_thread(c, jac::unpack_dev(c->I, c->J, c->K, c->prec, JAC_P, c->pbuf[c->cur], p_dev, c->stream));
+}
+
+jac_status jac_download(jac_ctx *c, double *p_host)
+{
+    if (!c || !p_host) return ctx_fail(c, JAC_EINVAL, "NULL argument");
+    jac_status s = jac_download_dev(c, c ? c->staging : nullptr);
+    if (s != JAC_OK) return s;
+    const size_t n = (size_t)c->I * c->J * c->K;
+    cudaError_t e = cudaMemcpyAsync(p_host, c->staging, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return ctx_cuda(c, e, "device-to-host copy");
+    s = jac::workspace_check(c->ws, c->stream);  // synchronises
+    return ctx_from_thread(c, s);
+}
+
+jac_status jac_sweep_count(const jac_ctx *c, long long *out)
+{
+    if (!c || !out) return JAC_EINVAL;
+    *out = c->count;
+    return JAC_OK;
+}
+
+jac_status jac_get_grid(const jac_ctx *c, jac_grid *g)
+{
+    if (!c || !g) return JAC_EINVAL;
+    *g = make_grid(c);
+    return JAC_OK;
+}
+
+jac_status jac_sweep_unhoisted(jac_ctx *c, int n_iter, const jac_fields *host, double *p_host)
+{
+    if (!c || !host || !p_host) return ctx_fail(c, JAC_EINVAL, "NULL argument");
+    if (n_iter < 0) return ctx_fail(c, JAC_EINVAL, "n_iter must be >= 0");
+    jac_fields f = *host;
+    f.f[JAC_P] = p_host;
+    for (int t = 0; t < n_iter; ++t) {
+        jac_status s = upload_impl(c, &f, false);
+        if (s == JAC_OK) s = jac_sweep(c, 1);
+        if (s == JAC_OK) s = jac_download(c, p_host);
+        if (s != JAC_OK) return s;
+    }
+    c->count = n_iter;
+    return JAC_OK;
+}
+
+}  // extern "C"

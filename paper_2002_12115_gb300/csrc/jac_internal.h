@@ -1,0 +1,25 @@
+// Internal interfaces shared by the translation units of libjac.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/jacobi.h"
+
+namespace jac {
+
+const char *thread_last_error();
+void set_thread_error(const std::string &m);
+
+jac_status validate_grid(const jac_grid *g);
+jac_plan resolve_plan(const jac_grid *g, const jac_plan *plan);
+size_t sweep_workspace_bytes(const jac_grid *g, const jac_plan &p);
+jac_status sweep_dev(const jac_grid *g, const jac_plan *plan, int n_iter, double *d_residual, void *workspace,
+                     size_t ws_bytes, void *stream);
+jac_status pack_dev(int I, int J, int K, jac_prec prec, int which, const double *src, void *dst, cudaStream_t st);
+jac_status unpack_dev(int I, int J, int K, jac_prec prec, int which, const void *src, double *dst,
+                      cudaStream_t st);
+jac_status workspace_check(void *workspace, cudaStream_t st);
+
+}  // namespace jac
