@@ -147,7 +147,7 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------- oracle arm
-def oracle_sample(w: dict, min_seconds: float = 10.0, max_sweeps: int = 400, chunk: int = 10):
+def oracle_sample(w: dict, min_seconds: float = 10.0, max_sweeps: int = 4000, chunk: int = 10):
     """The FP64 CPU oracle, as it stands, on the workload's grid: sweeps in
     chunks until about min_seconds of CPU time; returns Gpt/s and details."""
     import jacobi_inputs as ji
