@@ -145,6 +145,39 @@ jac_status jac_pack_dev(int I, int J, int K, jac_prec prec, int which,
 jac_status jac_unpack_dev(int I, int J, int K, jac_prec prec, int which,
                           const void *d_src, double *d_dst, void *stream);
 
+/* Largest launch (CTAs of the last sweep) that jac_sweep_dev_noalloc serves:
+ * its scratch is 256 + 8 * JAC_NOALLOC_MAX_CTAS bytes (about 128 KiB). */
+#define JAC_NOALLOC_MAX_CTAS 16384
+
+/* jac_sweep_dev without a workspace argument, for callers that cannot
+ * allocate device memory: a plugin whose host application owns the GPU's
+ * memory through its own pool and passes in only input and output buffers,
+ * or a loop that cannot take the device-wide synchronisation cudaMalloc and
+ * cudaFree may cause.  The paper has no counterpart; this is an interface
+ * addition of this library.
+ *
+ * Same grid, plan, n_iter, d_residual and stream meaning as jac_sweep_dev.
+ * The scratch lives in one fixed array of this library's device memory, held
+ * on every GPU that loads the library until the process exits.  The call
+ * allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ *   - The first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress, with the device current); make that first call
+ *     before any stream capture on the device.
+ *   - Every call shares the array and overwrites what the previous call left
+ *     there; its header is cleared (cudaMemsetAsync) at the start of each
+ *     call.  Calls that overlap on the GPU (other streams, other host threads)
+ *     race on it: serialise them.
+ *   - Pass d_residual (device memory) to receive the residual; with NULL it
+ *     lands in the shared array and is lost to the next call.
+ *   - A bounded device wait that gives up is recorded only in the shared
+ *     array and is not reported; callers who need that report use
+ *     jac_sweep_dev with their own workspace and jac_workspace_check.
+ * Errors: as jac_sweep_dev, plus JAC_EINVAL when the launch would need more
+ * than JAC_NOALLOC_MAX_CTAS CTAs (choose a larger kdepth), and JAC_ECUDA if
+ * the array's address cannot be obtained. */
+jac_status jac_sweep_dev_noalloc(const jac_grid *g, const jac_plan *plan, int n_iter,
+                                 double *d_residual, void *stream);
+
 /* =====================================================================
  * Context API: one grid, resident in device memory owned by the context.
  * ===================================================================== */

@@ -56,6 +56,7 @@ _SIG = {
     "jac_sweep_dev": (_I, [ctypes.POINTER(jac_grid), ctypes.POINTER(jac_plan), _I, _VP, _VP,
                            ctypes.c_size_t, _VP]),
     "jac_workspace_check": (_I, [_VP, _VP]),
+    "jac_sweep_dev_noalloc": (_I, [ctypes.POINTER(jac_grid), ctypes.POINTER(jac_plan), _I, _VP, _VP]),
     "jac_pack_dev": (_I, [_I, _I, _I, _I, _I, _VP, _VP, _VP]),
     "jac_unpack_dev": (_I, [_I, _I, _I, _I, _I, _VP, _VP, _VP]),
     "jac_create": (_I, [ctypes.POINTER(_VP), _I, _I, _I, _I, ctypes.c_double, _VP]),

@@ -1,0 +1,129 @@
+"""jac_sweep_dev_noalloc against jac_sweep_dev, through the C ABI.
+
+jac_sweep_dev_noalloc serves callers that may not allocate device memory (a
+plugin handed only input and output buffers by a host that owns the GPU's
+memory, or a loop that cannot take cudaMalloc's synchronisation): it keeps
+its scratch in a fixed array inside the library instead of a caller
+workspace.  Two calls in a row must give what the workspace entry point
+gives, within the parity tolerance of each precision.  This file is
+collected last on purpose.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import jacobi_inputs as ji
+from _util import TOL
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("p", "a0", "a1", "a2", "a3", "b0", "b1", "b2", "c0", "c1", "c2", "wrk1", "bnd")
+PRECS = {"f64": 0, "f32": 1, "bf16": 2}
+
+
+def _elem(prec, name):
+    if prec == "f64":
+        return 8
+    if prec == "f32" or name in ("p", "wrk1"):
+        return 4
+    return 2
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2002_12115_gb300 import _build
+    _build.build()
+    import paper_2002_12115_gb300 as pkg
+    return pkg
+
+
+class Grid:
+    """Storage-layout buffers of one grid, owned by torch (the caller)."""
+
+    def __init__(self, pkg, fields, prec, omega=0.8):
+        import torch
+        K, J, I = fields["p"].shape
+        self.pkg, self.I, self.J, self.K, self.prec = pkg, I, J, K, prec
+        self.stream = torch.cuda.current_stream()
+        self.sh = pkg.stream_handle(self.stream)
+        pitch = pkg.pitch(I)
+        self.src = {n: torch.from_numpy(np.ascontiguousarray(v)).cuda() for n, v in fields.items()}
+        self.buf = {n: torch.zeros(pitch * J * K * _elem(prec, n), dtype=torch.uint8, device="cuda")
+                    for n in FIELDS}
+        self.p1 = torch.zeros_like(self.buf["p"])
+        g = pkg.jac_grid()
+        g.I, g.J, g.K, g.prec, g.omega = I, J, K, PRECS[prec], omega
+        g.p[0], g.p[1] = self.buf["p"].data_ptr(), self.p1.data_ptr()
+        for q, n in enumerate(FIELDS):
+            if q:
+                g.coef[q] = self.buf[n].data_ptr()
+        self.g = g
+        self.reset()
+
+    def reset(self):
+        lib = self.pkg.lib()
+        for q, n in enumerate(FIELDS):
+            st = lib.jac_pack_dev(self.I, self.J, self.K, PRECS[self.prec], q, self.src[n].data_ptr(),
+                                  self.buf[n].data_ptr(), ctypes.c_void_p(self.sh))
+            self.pkg.check(st)
+        self.p1.copy_(self.buf["p"])
+
+    def state(self, n):
+        import torch
+        out = torch.empty((self.K, self.J, self.I), dtype=torch.float64, device="cuda")
+        src = self.buf["p"] if n % 2 == 0 else self.p1
+        self.pkg.check(self.pkg.lib().jac_unpack_dev(self.I, self.J, self.K, PRECS[self.prec], 0,
+                                                     src.data_ptr(), out.data_ptr(), ctypes.c_void_p(self.sh)))
+        return out.cpu().numpy()
+
+
+def _with_workspace(pkg, grid, n, plan):
+    import torch
+    ws_bytes = pkg.workspace_size(grid.g, *plan)
+    ws = torch.zeros(ws_bytes, dtype=torch.uint8, device="cuda")
+    res = torch.zeros(1, dtype=torch.float64, device="cuda")
+    pkg.sweep_dev(grid.g, n, res.data_ptr(), ws.data_ptr(), ws_bytes, grid.sh, *plan)
+    return grid.state(n), float(res.item())
+
+
+def _no_alloc(pkg, grid, n, plan):
+    import torch
+    res = torch.zeros(1, dtype=torch.float64, device="cuda")
+    st = pkg.lib().jac_sweep_dev_noalloc(ctypes.byref(grid.g), ctypes.byref(pkg.jac_plan(*plan)), n,
+                                         ctypes.c_void_p(res.data_ptr()), ctypes.c_void_p(grid.sh))
+    pkg.check(st)
+    return grid.state(n), float(res.item())
+
+
+@pytest.mark.parametrize("prec,dims,n,plan", [("f32", (130, 37, 41), 7, (8, 5)),
+                                              ("bf16", (67, 29, 33), 4, (4, 3)),
+                                              ("f64", (70, 21, 19), 5, (16, 0))])
+def test_no_alloc_matches_workspace_entry_point(L, prec, dims, n, plan):
+    I, J, K = dims
+    grid = Grid(L, ji.himeno_fields(I, J, K, seed=200 + I), prec)
+    want_p, want_g = _with_workspace(L, grid, n, plan)
+    for call in range(2):                      # two calls in a row share the scratch
+        grid.reset()
+        p, g = _no_alloc(L, grid, n, plan)
+        err_p = np.abs(p - want_p).max() / np.abs(want_p).max()
+        err_g = abs(g - want_g) / abs(want_g)
+        assert err_p <= TOL[prec] and err_g <= TOL[prec], (call, err_p, err_g)
+
+
+def test_no_alloc_rejects_launch_beyond_its_scratch(L):
+    """130 x 1000 x 130 with one plane per CTA needs 64000 CTAs: rejected
+    before anything is launched."""
+    import paper_2002_12115_gb300 as pkg
+    I, J, K = 130, 1000, 130
+    f = {n: np.zeros((K, J, I)) for n in FIELDS}
+    f["bnd"] = ji.interior_mask(I, J, K)
+    grid = Grid(L, f, "f32")
+    res = ctypes.c_void_p(0)
+    st = L.lib().jac_sweep_dev_noalloc(ctypes.byref(grid.g), ctypes.byref(pkg.jac_plan(4, 1)), 1, res,
+                                       ctypes.c_void_p(grid.sh))
+    assert st == 1                              # JAC_EINVAL
+    assert b"at most 16384" in L.lib().jac_last_error(None)
