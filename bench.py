@@ -229,8 +229,8 @@ def run_native(args, w):
     p_dev = torch.empty((K, J, I), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
     jac = Jacobi(I, J, K, prec, 0.8, stream)
-    if args.tile_j or args.kdepth:
-        jac.set_plan(args.tile_j, args.kdepth)
+    if args.tile_j or args.kdepth or args.tile_i:
+        jac.set_plan(args.tile_j, args.kdepth, args.tile_i)
 
     sweep_ms = []
 
@@ -363,11 +363,15 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="config2")
     ap.add_argument("--tile-j", type=int, default=0)
     ap.add_argument("--kdepth", type=int, default=0)
+    ap.add_argument("--tile-i", type=int, default=0)
+    ap.add_argument("--sweeps", type=int, default=0, help="override the workload's sweep count (profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     args = ap.parse_args()
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.sweeps:
+        w["sweeps"] = args.sweeps
     if args.impl == "reference":
         run_reference(args, w)
     else:

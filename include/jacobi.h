@@ -109,11 +109,17 @@ typedef struct jac_grid {
     const void *coef[JAC_NFIELDS];
 } jac_grid;
 
-/* Launch shape of the sweep kernel: rows per CTA (tile_j, one warp per
- * row of 32 vectors) and k-planes per CTA (kdepth).  {0, 0} picks defaults. */
+/* Launch shape of the sweep kernel.  A work item is tile_i x tile_j points
+ * in (i, j) over kdepth consecutive k-planes; one consumer warp per j-row.
+ * Zero fields pick defaults (FP64 64 x 8, FP32 128 x 8, BF16 coefficients
+ * 128 x 16, kdepth for about 12 items per SM).  Supported shapes
+ * (tile_i x tile_j): FP64 64x4, 64x8; FP32 128x4, 128x8, 64x8, 64x16; BF16
+ * coefficients 128x4, 128x8, 128x16, 64x8, 64x16.  Others: JAC_EINVAL at
+ * launch. */
 typedef struct jac_plan {
-    int tile_j;   /* 4, 8 or 16 */
-    int kdepth;   /* >= 1 */
+    int tile_j;   /* rows per work item: 4, 8 or 16 */
+    int kdepth;   /* k-planes per work item, >= 1 */
+    int tile_i;   /* points per row: 64 or 128 */
 } jac_plan;
 
 /* Bytes of device workspace jac_sweep_dev needs for this grid and plan. */
@@ -145,9 +151,10 @@ jac_status jac_pack_dev(int I, int J, int K, jac_prec prec, int which,
 jac_status jac_unpack_dev(int I, int J, int K, jac_prec prec, int which,
                           const void *d_src, double *d_dst, void *stream);
 
-/* Largest launch (CTAs of the last sweep) that jac_sweep_dev_noalloc serves:
- * its scratch is 256 + 8 * JAC_NOALLOC_MAX_CTAS bytes (about 128 KiB). */
-#define JAC_NOALLOC_MAX_CTAS 16384
+/* Largest launch (CTAs) that jac_sweep_dev_noalloc serves: its scratch is
+ * 256 + 8 * JAC_NOALLOC_MAX_CTAS bytes (16.6 KiB).  The sweep launches at
+ * most one CTA per SM, so every current GPU fits. */
+#define JAC_NOALLOC_MAX_CTAS 2048
 
 /* jac_sweep_dev without a workspace argument, for callers that cannot
  * allocate device memory: a plugin whose host application owns the GPU's
@@ -173,8 +180,8 @@ jac_status jac_unpack_dev(int I, int J, int K, jac_prec prec, int which,
  *     array and is not reported; callers who need that report use
  *     jac_sweep_dev with their own workspace and jac_workspace_check.
  * Errors: as jac_sweep_dev, plus JAC_EINVAL when the launch would need more
- * than JAC_NOALLOC_MAX_CTAS CTAs (choose a larger kdepth), and JAC_ECUDA if
- * the array's address cannot be obtained. */
+ * than JAC_NOALLOC_MAX_CTAS CTAs (a device with more SMs than that), and
+ * JAC_ECUDA if the array's address cannot be obtained. */
 jac_status jac_sweep_dev_noalloc(const jac_grid *g, const jac_plan *plan, int n_iter,
                                  double *d_residual, void *stream);
 

@@ -14,8 +14,9 @@ namespace jac {
 // Layout of the first 256 bytes of every sweep workspace.
 struct WsHeader {
     int errword;          // JAC_OK or JAC_ETIMEOUT, written by kernels
-    unsigned counter;     // arrival counter of the residual's last-block reduction
-    unsigned pad0[2];
+    unsigned counter;     // CTAs finished (last one reduces and resets)
+    unsigned gbar;        // grid barrier between sweeps of one launch
+    unsigned pad0;
     double residual;      // default destination of the residual
 };
 constexpr size_t kWsHeaderBytes = 256;
@@ -65,6 +66,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Programmatic dependent launch: let the next kernel in the stream start its
+// prologue, and wait until the previous one has completed and its writes are
+// visible.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Wait for the phase with the given parity to complete; gives up after
 // kWaitLimitNs and returns false.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
@@ -73,6 +85,35 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     const unsigned long long t0 = globaltimer_ns();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+    }
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Order this thread's generic-proxy global accesses with later async-proxy
+// (TMA) accesses, in both directions.
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+// Named barrier over `count` threads (id 1; id 0 is __syncthreads).
+__device__ __forceinline__ void named_barrier_sync(int id, int count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Wait until *p >= target (acquire); false after kWaitLimitNs.
+__device__ __forceinline__ bool wait_counter_bounded(const unsigned *p, unsigned target)
+{
+    if (ld_acquire_gpu(p) >= target) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    while (true) {
+        __nanosleep(64);
+        if (ld_acquire_gpu(p) >= target) return true;
         if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
     }
 }

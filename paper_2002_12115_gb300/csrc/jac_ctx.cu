@@ -26,7 +26,7 @@ struct jac_ctx {
     double *staging = nullptr;        // I*J*K doubles
     void *ws = nullptr;               // sweep workspace
     size_t ws_bytes = 0;
-    jac_plan plan{0, 0};
+    jac_plan plan{0, 0, 0};
     long long count = 0;
     bool uploaded = false;
     bool has_res = false;
@@ -196,10 +196,12 @@ const char *jac_last_error(const jac_ctx *c) { return c ? c->err.c_str() : jac::
 jac_status jac_set_plan(jac_ctx *c, const jac_plan *plan)
 {
     if (!c) return ctx_fail(c, JAC_EINVAL, "ctx is NULL");
-    jac_plan p{0, 0};
+    jac_plan p{0, 0, 0};
     if (plan) p = *plan;
     if (p.tile_j != 0 && p.tile_j != 4 && p.tile_j != 8 && p.tile_j != 16)
         return ctx_fail(c, JAC_EINVAL, "tile_j must be 0, 4, 8 or 16");
+    if (p.tile_i != 0 && p.tile_i != 64 && p.tile_i != 128)
+        return ctx_fail(c, JAC_EINVAL, "tile_i must be 0, 64 or 128");
     if (p.kdepth < 0) return ctx_fail(c, JAC_EINVAL, "kdepth must be >= 0");
     c->plan = p;
     return ensure_workspace(c);
