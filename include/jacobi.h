@@ -241,6 +241,51 @@ jac_status jac_sweep_count(const jac_ctx *ctx, long long *out);
  * handled by the context; g->p[0] is the current state after this call). */
 jac_status jac_get_grid(const jac_ctx *ctx, jac_grid *g);
 
+/* ---------------------------------------------------------------------
+ * Adjoint (reverse mode).  For a terminal loss L(p_T), the adjoint of one
+ * sweep maps lambda_{t+1} = dL/dp_{t+1} to lambda_t in gather form:
+ *   lambda_t[y] = lambda_{t+1}[y] - mu[y] + sum over the 18 neighbours x of y
+ *                 of w[x] * (coefficient of p[y] in the update of x),
+ * mu[x] = omega bnd[x] lambda_{t+1}[x] on interior x (0 on faces),
+ * w[x] = a3[x] mu[x]; its parameter gradients at interior x are
+ * dL/dwrk1 += w, dL/da3 += mu s0_t, dL/da0 += w p_t[i+1], dL/dc0 += w p_t[i-1]
+ * (and likewise a1, a2, c1, c2), dL/db0 += w * (b0 bracket of p_t), etc.
+ * Gradients accumulate in FP64; lambda is kept in the element type of p.
+ * There is no paper counterpart: this is the differentiation addition of
+ * this library (the sweep itself is the Himeno relaxation of Section 5.1.1).
+ * --------------------------------------------------------------------- */
+
+/* One adjoint sweep, stateless.  g describes the grid (coefficients; p[0]
+ * and p[1] unused).  p_t: the state before the sweep, lam_in: lambda_{t+1},
+ * lam_out: lambda_t (storage layout, element type of p; lam_out != lam_in;
+ * every point including faces is written).  g_wrk1, g_a3: dense FP64
+ * (I*J*K) arrays, accumulated (+=).  g_coef: NULL, or nine dense FP64
+ * arrays for a0, a1, a2, b0, b1, b2, c0, c1, c2, accumulated.  kdepth: planes
+ * per CTA (0: 16).  Asynchronous on stream. */
+jac_status jac_adjoint_step_dev(const jac_grid *g, const void *p_t, const void *lam_in, void *lam_out,
+                                double *g_wrk1, double *g_a3, double *const *g_coef, int kdepth,
+                                void *stream);
+
+/* Start a checkpoint tape: the next sweeps (at most max_sweeps, across any
+ * number of jac_sweep calls) are recorded by saving the state at the start
+ * of every C-sweep segment.  Allocates ceil(max_sweeps/C) + C + 2 state
+ * arrays.  A new upload or jac_tape_end discards the tape. */
+jac_status jac_tape_begin(jac_ctx *ctx, int C, int max_sweeps);
+jac_status jac_tape_end(jac_ctx *ctx);
+
+/* Sweeps recorded on the tape so far. */
+jac_status jac_tape_count(const jac_ctx *ctx, int *out);
+
+/* Reverse pass over the taped sweeps for a terminal adjoint lambda_T
+ * (dense FP64, device; e.g. p_T - target for L = 1/2 |p_T - target|^2).
+ * Each segment is recomputed from its checkpoint into C state buffers, then
+ * swept backwards.  Outputs (dense FP64, device, overwritten): g_wrk1,
+ * g_a3, and if not NULL the nine arrays of g_coef (a0 a1 a2 b0 b1 b2 c0 c1
+ * c2) and g_p0 = dL/d(state at tape start).  The forward state, count and
+ * residual are unchanged.  Asynchronous.  JAC_ESTATE without taped sweeps. */
+jac_status jac_sweep_adjoint(jac_ctx *ctx, const double *lambda_T, double *g_wrk1, double *g_a3,
+                             double *const *g_coef, double *g_p0);
+
 /* The contrast to hoisting, for measurement only: for each of n_iter
  * sweeps, copy all thirteen host arrays in (the current host state as p),
  * run one sweep, copy p back out to p_host.  On entry p_host holds p0; on

@@ -15,5 +15,14 @@ include/jacobi.h, with hand-written sm_103a CUDA kernels.
 from .binding import (FIELDS, PRECS, JacError, Jacobi, check, jac_fields, jac_grid, jac_plan, lib, pitch,
                       stream_handle, sweep_dev, workspace_size)
 
-__all__ = ["FIELDS", "PRECS", "JacError", "Jacobi", "check", "jac_fields", "jac_grid", "jac_plan", "lib",
-           "pitch", "stream_handle", "sweep_dev", "workspace_size"]
+
+def __getattr__(name):
+    # torch-dependent parts load lazily
+    if name in ("JacobiSweep", "jacobi_sweep"):
+        from . import autograd
+        return getattr(autograd, name)
+    raise AttributeError(name)
+
+
+__all__ = ["FIELDS", "PRECS", "JacError", "Jacobi", "JacobiSweep", "check", "jac_fields", "jac_grid",
+           "jac_plan", "jacobi_sweep", "lib", "pitch", "stream_handle", "sweep_dev", "workspace_size"]

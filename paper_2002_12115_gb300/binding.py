@@ -72,6 +72,11 @@ _SIG = {
     "jac_sweep_count": (_I, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
     "jac_get_grid": (_I, [_VP, ctypes.POINTER(jac_grid)]),
     "jac_sweep_unhoisted": (_I, [_VP, _I, ctypes.POINTER(jac_fields), _VP]),
+    "jac_adjoint_step_dev": (_I, [ctypes.POINTER(jac_grid), _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP]),
+    "jac_tape_begin": (_I, [_VP, _I, _I]),
+    "jac_tape_end": (_I, [_VP]),
+    "jac_tape_count": (_I, [_VP, ctypes.POINTER(_I)]),
+    "jac_sweep_adjoint": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
 }
 
 _lock = threading.Lock()
@@ -221,6 +226,41 @@ class Jacobi:
         g = jac_grid()
         self._check(lib().jac_get_grid(self._h, ctypes.byref(g)))
         return g
+
+    # -- reverse mode
+    def tape_begin(self, C: int, max_sweeps: int) -> None:
+        """Record the next sweeps (at most max_sweeps) with a checkpoint every C."""
+        self._check(lib().jac_tape_begin(self._h, int(C), int(max_sweeps)))
+
+    def tape_end(self) -> None:
+        self._check(lib().jac_tape_end(self._h))
+
+    def tape_count(self) -> int:
+        n = ctypes.c_int()
+        self._check(lib().jac_tape_count(self._h, ctypes.byref(n)))
+        return n.value
+
+    def sweep_adjoint(self, lam_T, coef_grads: bool = False, want_p0: bool = True) -> dict:
+        """Reverse pass over the taped sweeps.  lam_T: float64 CUDA tensor
+        (K, J, I) = dL/dp_T.  Returns FP64 tensors g_wrk1, g_a3 and, as
+        requested, g_p0 and g_a0..g_c2."""
+        import torch
+        if tuple(lam_T.shape) != self.shape or lam_T.dtype != torch.float64 or not lam_T.is_cuda:
+            raise ValueError(f"lam_T must be a float64 CUDA tensor of shape {self.shape}")
+        lam_T = lam_T.contiguous()
+        out = {"g_wrk1": torch.empty_like(lam_T), "g_a3": torch.empty_like(lam_T)}
+        gc = None
+        if coef_grads:
+            names = ("a0", "a1", "a2", "b0", "b1", "b2", "c0", "c1", "c2")
+            for nm in names:
+                out["g_" + nm] = torch.empty_like(lam_T)
+            gc = (_VP * 9)(*[out["g_" + nm].data_ptr() for nm in names])
+        if want_p0:
+            out["g_p0"] = torch.empty_like(lam_T)
+        self._check(lib().jac_sweep_adjoint(self._h, _VP(lam_T.data_ptr()), _VP(out["g_wrk1"].data_ptr()),
+                                            _VP(out["g_a3"].data_ptr()), gc,
+                                            _VP(out["g_p0"].data_ptr()) if want_p0 else None))
+        return out
 
     def sweep_unhoisted(self, n: int, fields: dict, p_host: np.ndarray) -> None:
         """Per-sweep copy-in / copy-out (measurement contrast only)."""

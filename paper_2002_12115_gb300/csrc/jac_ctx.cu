@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -31,6 +32,17 @@ struct jac_ctx {
     bool uploaded = false;
     bool has_res = false;
     std::string err;
+    // checkpoint tape of the sweeps since jac_tape_begin
+    struct Tape {
+        int C = 0, max_sweeps = 0, taped = 0;
+        void *mem = nullptr;      // checkpoints, segment states, two lambda buffers, one double
+        size_t state_bytes = 0;
+        int n_ckpt = 0;
+        char *ckpt(int s) const { return static_cast<char *>(mem) + (size_t)s * state_bytes; }
+        char *seg(int m) const { return ckpt(n_ckpt) + (size_t)m * state_bytes; }
+        char *lam(int b) const { return seg(C) + (size_t)b * state_bytes; }
+        double *scratch() const { return reinterpret_cast<double *>(lam(2)); }
+    } tape;
 };
 
 namespace {
@@ -91,6 +103,47 @@ jac_status ensure_workspace(jac_ctx *c)
     return JAC_OK;
 }
 
+void tape_free(jac_ctx *c)
+{
+    if (c->tape.mem) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->tape.mem);
+    }
+    c->tape = jac_ctx::Tape();
+}
+
+// Sweeps on the resident state; while a tape is active, the state at the
+// start of every C-sweep segment is saved first.
+jac_status sweep_impl(jac_ctx *c, int n_iter)
+{
+    jac_status s = ensure_workspace(c);
+    if (s != JAC_OK) return s;
+    jac::WsHeader *hdr = static_cast<jac::WsHeader *>(c->ws);
+    jac_ctx::Tape &tp = c->tape;
+    if (tp.mem && tp.taped + n_iter > tp.max_sweeps)
+        return ctx_fail(c, JAC_ESTATE, "more sweeps than the tape was sized for");
+    while (n_iter > 0) {
+        int chunk = n_iter;
+        if (tp.mem) {
+            if (tp.taped % tp.C == 0) {
+                cudaError_t e = cudaMemcpyAsync(tp.ckpt(tp.taped / tp.C), c->pbuf[c->cur], tp.state_bytes,
+                                                cudaMemcpyDeviceToDevice, c->stream);
+                if (e != cudaSuccess) return ctx_cuda(c, e, "checkpoint copy");
+            }
+            chunk = std::min(n_iter, tp.C - tp.taped % tp.C);
+        }
+        jac_grid g = make_grid(c);
+        s = jac::sweep_dev(&g, &c->plan, chunk, &hdr->residual, c->ws, c->ws_bytes, c->stream);
+        if (s != JAC_OK) return ctx_from_thread(c, s);
+        c->cur = (c->cur + chunk) & 1;
+        c->count += chunk;
+        if (tp.mem) tp.taped += chunk;
+        n_iter -= chunk;
+    }
+    c->has_res = true;
+    return JAC_OK;
+}
+
 jac_status upload_impl(jac_ctx *c, const jac_fields *f, bool on_device)
 {
     if (!c) return ctx_fail(c, JAC_EINVAL, "ctx is NULL");
@@ -119,6 +172,7 @@ jac_status upload_impl(jac_ctx *c, const jac_fields *f, bool on_device)
     c->count = 0;
     c->uploaded = true;
     c->has_res = false;
+    tape_free(c);
     return JAC_OK;
 }
 
@@ -183,6 +237,7 @@ jac_status jac_create(jac_ctx **out, int I, int J, int K, jac_prec prec, double 
 jac_status jac_destroy(jac_ctx *c)
 {
     if (!c) return JAC_OK;
+    tape_free(c);
     cudaStreamSynchronize(c->stream);
     if (c->ws) cudaFree(c->ws);
     if (c->staging) cudaFree(c->staging);
@@ -217,16 +272,7 @@ jac_status jac_sweep(jac_ctx *c, int n_iter)
     if (!c->uploaded) return ctx_fail(c, JAC_ESTATE, "jac_sweep before jac_upload");
     if (n_iter < 0) return ctx_fail(c, JAC_EINVAL, "n_iter must be >= 0");
     if (n_iter == 0) return JAC_OK;
-    jac_status s = ensure_workspace(c);
-    if (s != JAC_OK) return s;
-    jac_grid g = make_grid(c);
-    jac::WsHeader *hdr = static_cast<jac::WsHeader *>(c->ws);
-    s = jac::sweep_dev(&g, &c->plan, n_iter, &hdr->residual, c->ws, c->ws_bytes, c->stream);
-    if (s != JAC_OK) return ctx_from_thread(c, s);
-    c->cur = (c->cur + n_iter) & 1;
-    c->count += n_iter;
-    c->has_res = true;
-    return JAC_OK;
+    return sweep_impl(c, n_iter);
 }
 
 jac_status jac_residual(jac_ctx *c, double *out)
@@ -272,6 +318,90 @@ jac_status jac_get_grid(const jac_ctx *c, jac_grid *g)
 {
     if (!c || !g) return JAC_EINVAL;
     *g = make_grid(c);
+    return JAC_OK;
+}
+
+jac_status jac_tape_begin(jac_ctx *c, int C, int max_sweeps)
+{
+    if (!c) return ctx_fail(c, JAC_EINVAL, "ctx is NULL");
+    if (!c->uploaded) return ctx_fail(c, JAC_ESTATE, "jac_tape_begin before jac_upload");
+    if (C < 1 || max_sweeps < 1) return ctx_fail(c, JAC_EINVAL, "C and max_sweeps must be >= 1");
+    tape_free(c);
+    jac_ctx::Tape tp;
+    tp.C = std::min(C, max_sweeps);
+    tp.max_sweeps = max_sweeps;
+    tp.state_bytes = array_bytes(c, JAC_P);
+    tp.n_ckpt = (max_sweeps + tp.C - 1) / tp.C;
+    const size_t bytes = (size_t)(tp.n_ckpt + tp.C + 2) * tp.state_bytes + 256;
+    cudaError_t e = cudaMalloc(&tp.mem, bytes);
+    if (e != cudaSuccess) return ctx_fail(c, JAC_ENOMEM, "tape allocation failed (" + std::to_string(bytes) + " bytes)");
+    c->tape = tp;
+    return JAC_OK;
+}
+
+jac_status jac_tape_end(jac_ctx *c)
+{
+    if (!c) return ctx_fail(c, JAC_EINVAL, "ctx is NULL");
+    tape_free(c);
+    return JAC_OK;
+}
+
+jac_status jac_sweep_adjoint(jac_ctx *c, const double *lam_T, double *g_wrk1, double *g_a3, double *const *g_coef,
+                             double *g_p0)
+{
+    if (!c) return ctx_fail(c, JAC_EINVAL, "ctx is NULL");
+    jac_ctx::Tape &tp = c->tape;
+    if (!tp.mem || tp.taped == 0) return ctx_fail(c, JAC_ESTATE, "no taped sweeps: call jac_tape_begin, then jac_sweep");
+    if (!lam_T || !g_wrk1 || !g_a3) return ctx_fail(c, JAC_EINVAL, "lambda_T, g_wrk1 and g_a3 are required");
+    jac_status s = ensure_workspace(c);
+    if (s != JAC_OK) return s;
+    const size_t n = (size_t)c->I * c->J * c->K;
+    cudaError_t e = cudaMemsetAsync(g_wrk1, 0, n * sizeof(double), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g_a3, 0, n * sizeof(double), c->stream);
+    for (int q = 0; g_coef && q < 9 && e == cudaSuccess; ++q) {
+        if (!g_coef[q]) return ctx_fail(c, JAC_EINVAL, "g_coef needs all nine arrays");
+        e = cudaMemsetAsync(g_coef[q], 0, n * sizeof(double), c->stream);
+    }
+    if (e != cudaSuccess) return ctx_cuda(c, e, "gradient clear");
+    // lambda_T into storage layout
+    s = jac::pack_dev(c->I, c->J, c->K, c->prec, JAC_P, lam_T, tp.lam(0), c->stream);
+    if (s != JAC_OK) return ctx_from_thread(c, s);
+    // faces never change: give every segment slot the faces of the first checkpoint
+    for (int m = 0; m < tp.C; ++m) {
+        e = cudaMemcpyAsync(tp.seg(m), tp.ckpt(0), tp.state_bytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) return ctx_cuda(c, e, "segment init");
+    }
+    jac_grid g = make_grid(c);
+    int lc = 0;
+    const int nseg = (tp.taped + tp.C - 1) / tp.C;
+    for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+        const int t0 = sgi * tp.C;
+        const int len = std::min(tp.C, tp.taped - t0);
+        e = cudaMemcpyAsync(tp.seg(0), tp.ckpt(sgi), tp.state_bytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) return ctx_cuda(c, e, "checkpoint restore");
+        for (int m = 1; m < len; ++m) {          // recompute the segment's states
+            g.p[0] = tp.seg(m - 1);
+            g.p[1] = tp.seg(m);
+            s = jac::sweep_dev(&g, &c->plan, 1, tp.scratch(), c->ws, c->ws_bytes, c->stream);
+            if (s != JAC_OK) return ctx_from_thread(c, s);
+        }
+        for (int m = len - 1; m >= 0; --m) {     // reverse sweeps of the segment
+            s = jac::adjoint_step_dev(&g, tp.seg(m), tp.lam(lc), tp.lam(lc ^ 1), g_wrk1, g_a3, g_coef, 0, c->stream);
+            if (s != JAC_OK) return ctx_from_thread(c, s);
+            lc ^= 1;
+        }
+    }
+    if (g_p0) {
+        s = jac::unpack_dev(c->I, c->J, c->K, c->prec, JAC_P, tp.lam(lc), g_p0, c->stream);
+        if (s != JAC_OK) return ctx_from_thread(c, s);
+    }
+    return JAC_OK;
+}
+
+jac_status jac_tape_count(const jac_ctx *c, int *out)
+{
+    if (!c || !out) return JAC_EINVAL;
+    *out = c->tape.mem ? c->tape.taped : 0;
     return JAC_OK;
 }
 

@@ -21,5 +21,7 @@ jac_status pack_dev(int I, int J, int K, jac_prec prec, int which, const double 
 jac_status unpack_dev(int I, int J, int K, jac_prec prec, int which, const void *src, double *dst,
                       cudaStream_t st);
 jac_status workspace_check(void *workspace, cudaStream_t st);
+jac_status adjoint_step_dev(const jac_grid *g, const void *p_t, const void *lam_in, void *lam_out, double *g_wrk1,
+                            double *g_a3, double *const *g_coef, int kdepth, cudaStream_t st);
 
 }  // namespace jac
