@@ -110,16 +110,18 @@ typedef struct jac_grid {
 } jac_grid;
 
 /* Launch shape of the sweep kernel.  A work item is tile_i x tile_j points
- * in (i, j) over kdepth consecutive k-planes; one consumer warp per j-row.
- * Zero fields pick defaults (FP64 64 x 8, FP32 128 x 8, BF16 coefficients
- * 128 x 16, kdepth for about 12 items per SM).  Supported shapes
- * (tile_i x tile_j): FP64 64x4, 64x8; FP32 128x4, 128x8, 64x8, 64x16; BF16
- * coefficients 128x4, 128x8, 128x16, 64x8, 64x16.  Others: JAC_EINVAL at
- * launch. */
+ * in (i, j) over kdepth consecutive k-planes.  The kernel runs W consumer
+ * warps; each covers tile_j / W rows of tile_i points (so W = tile_j * tile_i
+ * / 128 for FP32/BF16, tile_j * tile_i / 64 for FP64).  tile_i: a power of
+ * two in [16, 128] (FP64: [16, 64]); W must be 4 or 8, or 16 with BF16
+ * coefficients and tile_i >= 32.  Zero fields pick defaults: W = 8 (16 for
+ * BF16 on grids a 128-wide tile covers fully), the tile width with the best
+ * lane use, and kdepth for about 12 work items per SM.  Unsupported shapes:
+ * JAC_EINVAL at launch. */
 typedef struct jac_plan {
-    int tile_j;   /* rows per work item: 4, 8 or 16 */
+    int tile_j;   /* rows per work item */
     int kdepth;   /* k-planes per work item, >= 1 */
-    int tile_i;   /* points per row: 64 or 128 */
+    int tile_i;   /* points per row */
 } jac_plan;
 
 /* Bytes of device workspace jac_sweep_dev needs for this grid and plan. */
@@ -285,6 +287,56 @@ jac_status jac_tape_count(const jac_ctx *ctx, int *out);
  * residual are unchanged.  Asynchronous.  JAC_ESTATE without taped sweeps. */
 jac_status jac_sweep_adjoint(jac_ctx *ctx, const double *lambda_T, double *g_wrk1, double *g_a3,
                              double *const *g_coef, double *g_p0);
+
+/* ---------------------------------------------------------------------
+ * Batched grids: many independent grids of uneven sizes swept together in
+ * one persistent launch (a CUDA graph replayed on every call), each grid in
+ * its own device storage.  No paper counterpart: the paper offloads one
+ * application at a time; this serves many small Himeno-style problems.
+ * --------------------------------------------------------------------- */
+typedef struct jac_batch jac_batch;
+
+/* n grids, dims[3g..3g+2] = I, J, K of grid g (each >= 3).  Allocates every
+ * grid's storage (cudaMalloc), a staging array of the largest grid and n
+ * residuals.  stream: the cudaStream_t of every call. */
+jac_status jac_batch_create(jac_batch **out, int n, const int *dims, jac_prec prec, double omega,
+                            void *stream);
+jac_status jac_batch_destroy(jac_batch *b);
+const char *jac_batch_last_error(const jac_batch *b);
+
+/* Hoisted copy-in of grid g (host or device dense FP64 arrays, as for
+ * jac_upload / jac_upload_dev). */
+jac_status jac_batch_upload(jac_batch *b, int g, const jac_fields *host);
+jac_status jac_batch_upload_dev(jac_batch *b, int g, const jac_fields *dev);
+
+/* Launch plan: `warps` consumer warps per CTA for the whole launch (4 or 8;
+ * 16 with BF16 coefficients; 0 = 8) and per grid a tile width tile_i[g] (a
+ * power of two in [16, 128] for FP32/BF16, [16, 64] for FP64; 0 = the width
+ * with the best lane use) and k-block depth kdepth[g] (0 = default).  NULL
+ * arrays mean all defaults.  The next sweep rebuilds the device tables. */
+jac_status jac_batch_set_plan(jac_batch *b, int warps, const int *tile_i, const int *kdepth);
+
+/* The plan grid g will run with (after defaults). */
+jac_status jac_batch_grid_plan(const jac_batch *b, int g, jac_plan *out);
+
+/* n_iter sweeps of every grid in one persistent launch (captured in a CUDA
+ * graph on first use for this n_iter and buffer parity, then replayed).
+ * If res_host is not NULL it receives the n residuals of the last sweep.
+ * Synchronises.  JAC_ETIMEOUT if a bounded device wait gave up. */
+jac_status jac_batch_sweep(jac_batch *b, int n_iter, double *res_host);
+
+/* The same sweeps as a loop of per-grid launches, for comparison: one
+ * cooperative launch of n_iter sweeps per grid (per_sweep = 0), or one
+ * launch per sweep per grid (per_sweep != 0). */
+jac_status jac_batch_sweep_loop(jac_batch *b, int n_iter, int per_sweep, double *res_host);
+
+/* Current state of grid g as dense FP64 (host: synchronises; device: async). */
+jac_status jac_batch_download(jac_batch *b, int g, double *p_host);
+jac_status jac_batch_download_dev(jac_batch *b, int g, double *p_dev);
+
+/* Work items and CTAs of the current plan (0 before the first sweep), the
+ * warp count and the sweeps run so far. */
+jac_status jac_batch_info(const jac_batch *b, int *n_items, int *n_ctas, int *warps, long long *sweeps);
 
 /* The contrast to hoisting, for measurement only: for each of n_iter
  * sweeps, copy all thirteen host arrays in (the current host state as p),

@@ -190,3 +190,63 @@ def fd_points(I: int, J: int, K: int, count: int = 64) -> tuple[np.ndarray, np.n
     points for wrk1, then ``count`` for a3, from the stream seeded with FD_SEED."""
     pts = interior_points(I, J, K, 2 * count, FD_SEED)
     return pts[:count], pts[count:]
+
+
+# ------------------------------------------------------------------ torch
+# The same recipe with torch tensors (for example on the GPU, where large
+# workloads are generated in seconds).  SplitMix64 is evaluated in int64
+# two's-complement arithmetic: products wrap modulo 2^64 exactly as for
+# uint64, and the logical right shifts are arithmetic shifts with the sign
+# bits masked off.  Bit-identical to the numpy version (tested).
+def _as_i64(u: int) -> int:
+    u &= _MASK64
+    return u - (1 << 64) if u >= (1 << 63) else u
+
+
+def _torch_mix(z):
+    import torch
+    z = (z ^ ((z >> 30) & ((1 << 34) - 1))) * _as_i64(0xBF58476D1CE4E5B9)
+    z = (z ^ ((z >> 27) & ((1 << 37) - 1))) * _as_i64(0x94D049BB133111EB)
+    return z ^ ((z >> 31) & ((1 << 33) - 1))
+
+
+def uniform_torch(seed: int, start: int, count: int, lo: float, hi: float, device="cuda", chunk: int = 1 << 26):
+    """U[lo, hi) draws start+1 .. start+count as a float64 torch tensor."""
+    import torch
+    out = torch.empty(count, dtype=torch.float64, device=device)
+    g = _as_i64(0x9E3779B97F4A7C15)
+    s = _as_i64(seed)
+    for c0 in range(0, count, chunk):
+        c1 = min(count, c0 + chunk)
+        n = torch.arange(start + c0 + 1, start + c1 + 1, dtype=torch.int64, device=device)
+        z = _torch_mix(n * g + s)
+        u = ((z >> 11) & ((1 << 53) - 1)).to(torch.float64) * (1.0 / 9007199254740992.0)
+        out[c0:c1] = lo + (hi - lo) * u
+    return out
+
+
+def himeno_fields_torch(I: int, J: int, K: int, seed: int = SEED, device="cuda") -> dict:
+    """himeno_fields as float64 torch tensors of shape (K, J, I) on `device`."""
+    import torch
+    if min(I, J, K) < 3:
+        raise ValueError("every grid dimension must be at least 3")
+    N = I * J * K
+    f = {}
+    for q, name in enumerate(DRAW_ORDER):
+        lo, hi = _RANGES[name]
+        f[name] = uniform_torch(seed, q * N, N, lo, hi, device).view(K, J, I)
+    s = f["a0"] + f["a1"]
+    s += f["a2"]
+    s += f["c0"]
+    s += f["c1"]
+    s += f["c2"]
+    f["a3"] = torch.reciprocal(s)
+    del s
+    kk = torch.arange(K, dtype=torch.float64, device=device) / float(K - 1)
+    p = f.pop("pnoise")
+    p += (kk * kk).view(K, 1, 1)
+    f["p"] = p
+    bnd = torch.zeros((K, J, I), dtype=torch.float64, device=device)
+    bnd[1:K - 1, 1:J - 1, 1:I - 1] = 1.0
+    f["bnd"] = bnd
+    return {name: f[name] for name in FIELD_NAMES}

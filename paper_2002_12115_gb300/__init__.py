@@ -12,7 +12,7 @@ include/jacobi.h, with hand-written sm_103a CUDA kernels.
         gosa = jac.residual()     # residual of the last sweep
         p = jac.download()        # one copy-out
 """
-from .binding import (FIELDS, PRECS, JacError, Jacobi, check, jac_fields, jac_grid, jac_plan, lib, pitch,
+from .binding import (FIELDS, PRECS, JacError, Jacobi, JacobiBatch, check, jac_fields, jac_grid, jac_plan, lib, pitch,
                       stream_handle, sweep_dev, workspace_size)
 
 
@@ -24,5 +24,5 @@ def __getattr__(name):
     raise AttributeError(name)
 
 
-__all__ = ["FIELDS", "PRECS", "JacError", "Jacobi", "JacobiSweep", "check", "jac_fields", "jac_grid",
+__all__ = ["FIELDS", "PRECS", "JacError", "Jacobi", "JacobiBatch", "JacobiSweep", "check", "jac_fields", "jac_grid",
            "jac_plan", "jacobi_sweep", "lib", "pitch", "stream_handle", "sweep_dev", "workspace_size"]

@@ -77,6 +77,19 @@ _SIG = {
     "jac_tape_end": (_I, [_VP]),
     "jac_tape_count": (_I, [_VP, ctypes.POINTER(_I)]),
     "jac_sweep_adjoint": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "jac_batch_create": (_I, [ctypes.POINTER(_VP), _I, _VP, _I, ctypes.c_double, _VP]),
+    "jac_batch_destroy": (_I, [_VP]),
+    "jac_batch_last_error": (ctypes.c_char_p, [_VP]),
+    "jac_batch_upload": (_I, [_VP, _I, ctypes.POINTER(jac_fields)]),
+    "jac_batch_upload_dev": (_I, [_VP, _I, ctypes.POINTER(jac_fields)]),
+    "jac_batch_set_plan": (_I, [_VP, _I, _VP, _VP]),
+    "jac_batch_grid_plan": (_I, [_VP, _I, ctypes.POINTER(jac_plan)]),
+    "jac_batch_sweep": (_I, [_VP, _I, _VP]),
+    "jac_batch_sweep_loop": (_I, [_VP, _I, _I, _VP]),
+    "jac_batch_download": (_I, [_VP, _I, _VP]),
+    "jac_batch_download_dev": (_I, [_VP, _I, _VP]),
+    "jac_batch_info": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                            ctypes.POINTER(ctypes.c_longlong)]),
 }
 
 _lock = threading.Lock()
@@ -281,3 +294,108 @@ def sweep_dev(grid: jac_grid, n: int, d_residual: int | None, workspace: int, ws
     check(lib().jac_sweep_dev(ctypes.byref(grid), ctypes.byref(jac_plan(tile_j, kdepth, tile_i)), int(n),
                               _VP(d_residual) if d_residual else None, _VP(workspace), ctypes.c_size_t(ws_bytes),
                               _VP(stream)))
+
+
+class JacobiBatch:
+    """Many independent grids of uneven sizes, swept together in one
+    persistent launch replayed from a CUDA graph (a jac_batch)."""
+
+    def __init__(self, dims, prec: str = "f32", omega: float = 0.8, stream=None):
+        import torch
+        if prec not in PRECS:
+            raise ValueError(f"prec must be one of {list(PRECS)}")
+        self.dims = [tuple(int(x) for x in d) for d in dims]
+        self.n, self.prec, self.omega = len(self.dims), prec, float(omega)
+        self._stream_obj = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = stream_handle(self._stream_obj)
+        flat = (ctypes.c_int * (3 * self.n))(*[x for d in self.dims for x in d])
+        h = _VP()
+        check(lib().jac_batch_create(ctypes.byref(h), self.n, ctypes.cast(flat, _VP), PRECS[prec], self.omega,
+                                     _VP(self.stream)))
+        self._h = h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().jac_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, st: int) -> None:
+        if st != JAC_OK:
+            msg = lib().jac_batch_last_error(self._h)
+            raise JacError(st, msg.decode() if msg else "")
+
+    def shape(self, g: int):
+        I, J, K = self.dims[g]
+        return (K, J, I)
+
+    def _fields(self, g: int, arrays: dict, device: bool) -> jac_fields:
+        f = jac_fields()
+        for q, name in enumerate(FIELDS):
+            a = arrays[name]
+            if tuple(a.shape) != self.shape(g):
+                raise ValueError(f"grid {g} {name}: expected shape {self.shape(g)}")
+            f.f[q] = a.data_ptr() if device else _host_ptr(a)
+        return f
+
+    def upload(self, g: int, fields: dict) -> None:
+        f = self._fields(g, fields, device=False)
+        self._check(lib().jac_batch_upload(self._h, int(g), ctypes.byref(f)))
+
+    def upload_tensors(self, g: int, fields: dict) -> None:
+        f = self._fields(g, fields, device=True)
+        self._check(lib().jac_batch_upload_dev(self._h, int(g), ctypes.byref(f)))
+
+    def set_plan(self, warps: int = 0, tile_i=None, kdepth=None) -> None:
+        ti = (ctypes.c_int * self.n)(*tile_i) if tile_i is not None else None
+        kd = (ctypes.c_int * self.n)(*kdepth) if kdepth is not None else None
+        self._check(lib().jac_batch_set_plan(self._h, int(warps), ctypes.cast(ti, _VP) if ti else None,
+                                             ctypes.cast(kd, _VP) if kd else None))
+
+    def grid_plan(self, g: int) -> tuple:
+        p = jac_plan()
+        self._check(lib().jac_batch_grid_plan(self._h, int(g), ctypes.byref(p)))
+        return (p.tile_i, p.tile_j, p.kdepth)
+
+    def sweep(self, n: int, residuals: bool = True):
+        """n sweeps of every grid in one persistent launch (graph replay)."""
+        out = np.empty(self.n) if residuals else None
+        self._check(lib().jac_batch_sweep(self._h, int(n), _VP(out.ctypes.data) if residuals else None))
+        return out
+
+    def sweep_loop(self, n: int, per_sweep: bool = False, residuals: bool = True):
+        """The same sweeps as per-grid launches (comparison)."""
+        out = np.empty(self.n) if residuals else None
+        self._check(lib().jac_batch_sweep_loop(self._h, int(n), int(bool(per_sweep)),
+                                               _VP(out.ctypes.data) if residuals else None))
+        return out
+
+    def download(self, g: int, out: np.ndarray | None = None) -> np.ndarray:
+        if out is None:
+            out = np.empty(self.shape(g), dtype=np.float64)
+        self._check(lib().jac_batch_download(self._h, int(g), _VP(_host_ptr(out))))
+        return out
+
+    def download_tensor(self, g: int, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.shape(g), dtype=torch.float64, device="cuda")
+        self._check(lib().jac_batch_download_dev(self._h, int(g), _VP(out.data_ptr())))
+        return out
+
+    def info(self) -> dict:
+        a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+        self._check(lib().jac_batch_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                         ctypes.byref(d)))
+        return {"items": a.value, "ctas": b.value, "warps": c.value, "sweeps": d.value}

@@ -253,11 +253,13 @@ jac_status jac_set_plan(jac_ctx *c, const jac_plan *plan)
     if (!c) return ctx_fail(c, JAC_EINVAL, "ctx is NULL");
     jac_plan p{0, 0, 0};
     if (plan) p = *plan;
-    if (p.tile_j != 0 && p.tile_j != 4 && p.tile_j != 8 && p.tile_j != 16)
-        return ctx_fail(c, JAC_EINVAL, "tile_j must be 0, 4, 8 or 16");
-    if (p.tile_i != 0 && p.tile_i != 64 && p.tile_i != 128)
-        return ctx_fail(c, JAC_EINVAL, "tile_i must be 0, 64 or 128");
-    if (p.kdepth < 0) return ctx_fail(c, JAC_EINVAL, "kdepth must be >= 0");
+    if (p.tile_j < 0 || p.tile_i < 0 || p.kdepth < 0) return ctx_fail(c, JAC_EINVAL, "negative plan entry");
+    if (p.tile_i || p.tile_j) {
+        jac_grid g = make_grid(c);
+        int rw = 0, tj = 0;
+        jac_status s = jac::check_plan(c->prec, jac::resolve_plan(&g, &p), &rw, &tj);
+        if (s != JAC_OK) return ctx_from_thread(c, s);
+    }
     c->plan = p;
     return ensure_workspace(c);
 }

@@ -9,6 +9,9 @@
 
 namespace jac {
 
+struct GridDesc;
+struct SweepArgs;
+
 const char *thread_last_error();
 void set_thread_error(const std::string &m);
 
@@ -21,6 +24,16 @@ jac_status pack_dev(int I, int J, int K, jac_prec prec, int which, const double 
 jac_status unpack_dev(int I, int J, int K, jac_prec prec, int which, const void *src, double *dst,
                       cudaStream_t st);
 jac_status workspace_check(void *workspace, cudaStream_t st);
+int device_sm_count();
+int vector_points(jac_prec prec);
+int max_row_fold(jac_prec prec, int tj);
+bool warps_supported(jac_prec prec, int tj);
+int best_tile_i(int I, int J, jac_prec prec, int tj);
+jac_status check_plan(jac_prec prec, const jac_plan &p, int *rw_out, int *tj_out);
+jac_status build_desc(GridDesc *d, const jac_grid *g, const jac_plan &p, int item_base);
+template <bool BATCH>
+jac_status launch_sweep(jac_prec prec, int tj, const GridDesc &d0, const SweepArgs &a, unsigned nblocks,
+                        cudaStream_t st);
 jac_status adjoint_step_dev(const jac_grid *g, const void *p_t, const void *lam_in, void *lam_out, double *g_wrk1,
                             double *g_a3, double *const *g_coef, int kdepth, cudaStream_t st);
 

@@ -32,3 +32,17 @@ def rel_p(p, q):
 
 def rel_g(g, h):
     return abs(g - h) / abs(h) if h != 0 else abs(g)
+
+
+def residual_ok(g, want, prec, n_int, pmax=1.0):
+    """The residual bar: relative TOL, except on grids so small (n_int < 64)
+    that a converged residual sits at the rounding level of the arithmetic.
+    There every ss carries an absolute rounding error up to about
+    delta = 16 eps |p|max, so the bar is the worst case of that error,
+    sum(2 |ss| delta + delta^2) <= 2 sqrt(n_int gosa) delta + n_int delta^2
+    (the state, which carries the real information, is still checked at TOL)."""
+    if rel_g(g, want) <= TOL[prec]:
+        return True
+    eps = 2.0 ** -53 if prec == "f64" else 2.0 ** -24
+    delta = 16 * eps * pmax
+    return n_int < 64 and abs(g - want) <= 2 * np.sqrt(n_int * abs(want)) * delta + n_int * delta ** 2

@@ -90,3 +90,15 @@ def test_fd_points_interior():
         assert pts[:, 0].min() >= 1 and pts[:, 0].max() <= 5
         assert pts[:, 1].min() >= 1 and pts[:, 1].max() <= 6
         assert pts[:, 2].min() >= 1 and pts[:, 2].max() <= 7
+
+
+def test_torch_generator_is_bit_identical():
+    torch = pytest.importorskip("torch")
+    I, J, K = 7, 6, 9
+    a = ji.himeno_fields(I, J, K, seed=42)
+    b = ji.himeno_fields_torch(I, J, K, seed=42, device="cpu")
+    for name in ji.FIELD_NAMES:
+        assert np.array_equal(a[name], b[name].numpy()), name
+    u = ji.uniform(123, 1000, 5000, -1.0, 1.0)
+    v = ji.uniform_torch(123, 1000, 5000, -1.0, 1.0, device="cpu", chunk=777).numpy()
+    assert np.array_equal(u, v)
