@@ -13,7 +13,8 @@ is kept and cached.
     descent over a tile width per size class (grid I) and a k-block depth
     per size class (grid K).
 
-Results are cached in a JSON file keyed by GPU name, precision and workload.
+Results are cached in a JSON file keyed by GPU name, precision and workload
+(by default autotune_cache.json next to this module).
 """
 from __future__ import annotations
 
@@ -25,9 +26,10 @@ from itertools import product
 
 from .binding import JacError
 
+# plans measured on this project's GPUs ship with the package; set
+# JAC_AUTOTUNE_CACHE to keep a cache elsewhere
 CACHE_PATH = os.environ.get("JAC_AUTOTUNE_CACHE",
-                            os.path.join(os.path.expanduser("~"), ".cache", "paper_2002_12115_gb300",
-                                         "autotune.json"))
+                            os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotune_cache.json"))
 
 
 def _gpu_name() -> str:
