@@ -129,6 +129,42 @@ __device__ __forceinline__ void tma_load_3d(void *smem_dst, const CUtensorMap *m
         : "memory");
 }
 
+// L2 cache policies for the copies and stores (createpolicy), by mode:
+// 0 = normal priority everywhere; 1 = keep the state in L2 (state copies and
+// stores evict_last, the streamed coefficients evict_first).
+__device__ __forceinline__ uint64_t l2_policy(int evict)
+{
+    uint64_t p;
+    if (evict > 0) asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    else if (evict < 0) asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    else asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// 3-D tiled TMA load with an L2 cache policy.
+__device__ __forceinline__ void tma_load_3d_hint(void *smem_dst, const CUtensorMap *map, uint64_t *bar, int x, int y,
+                                                 int z, uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(smem_u32(smem_dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z), "l"(policy)
+        : "memory");
+}
+
+__device__ __forceinline__ void st_v4_hint(float *p, float a, float b, float c, float d, uint64_t policy)
+{
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(a), "f"(b), "f"(c),
+                 "f"(d), "l"(policy)
+                 : "memory");
+}
+
+__device__ __forceinline__ void st_v2d_hint(double *p, double a, double b, uint64_t policy)
+{
+    asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(p), "d"(a), "d"(b), "l"(policy)
+                 : "memory");
+}
+
 // ---------------------------------------------------------------- loads
 // Streaming 16-byte / 8-byte loads of read-only data, not kept in L1.
 __device__ __forceinline__ float4 ld_stream_f4(const float *p)

@@ -25,6 +25,7 @@ jac_status unpack_dev(int I, int J, int K, jac_prec prec, int which, const void 
                       cudaStream_t st);
 jac_status workspace_check(void *workspace, cudaStream_t st);
 int device_sm_count();
+size_t device_l2_bytes();
 int vector_points(jac_prec prec);
 int max_row_fold(jac_prec prec, int tj);
 bool warps_supported(jac_prec prec, int tj);

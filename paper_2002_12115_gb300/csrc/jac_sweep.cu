@@ -128,6 +128,20 @@ const char *thread_last_error() { return g_err.c_str(); }
 void set_thread_error(const std::string &m) { g_err = m; }
 int device_sm_count() { return num_sms(); }
 
+size_t device_l2_bytes()
+{
+    static size_t l2 = 0;
+    if (l2 == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, dev) == cudaSuccess &&
+            v > 0)
+            l2 = (size_t)v;
+        else
+            l2 = 1;
+    }
+    return l2;
+}
+
 int vector_points(jac_prec prec) { return prec == JAC_F64 ? 2 : 4; }
 
 int max_row_fold(jac_prec prec, int tj)
@@ -356,6 +370,8 @@ jac_status sweep_dev(const jac_grid *g, const jac_plan *plan, int n_iter, double
     a.partials = reinterpret_cast<double *>(static_cast<char *>(workspace) + kWsHeaderBytes);
     a.res = d_residual ? d_residual : &hdr->residual;
     a.hdr = hdr;
+    const size_t state_bytes = 2 * (size_t)d0.pitch * g->J * g->K * (g->prec == JAC_F64 ? 8 : 4);
+    a.l2_keep_state = state_bytes <= device_l2_bytes() / 2;
     const unsigned nblocks = (unsigned)std::min<long long>(d0.nitems, num_sms());
     return launch_sweep<false>(g->prec, tj, d0, a, nblocks, static_cast<cudaStream_t>(stream));
 }
