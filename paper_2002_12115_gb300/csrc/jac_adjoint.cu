@@ -18,7 +18,9 @@
 // shared memory the nine products coef * w (with halo), p_t (with halo) and
 // the centre values needed for the gradients.  A plane is loaded into
 // registers one step ahead while the previous step computes, so global
-// latency overlaps the gather; a ring of three plane slots holds k-1, k, k+1.
+// latency overlaps the gather; a ring of three plane slots holds k-1, k, k+1
+// (a fourth slot with one barrier per plane was measured slower: the stores of
+// the next plane then contend with the gather for shared memory).
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -52,7 +54,8 @@ struct AdjShape {
     // centre tiles: lambda, mu, w, wrk1 and the nine raw coefficients
     enum { CLAM, CMU, CW, CWK, CA0, CA1, CA2, CB0, CB1, CB2, CC0, CC1, CC2, NCEN };
     static constexpr int SLOT = NHALO * HALO_TILE + NCEN * CEN_TILE;   // elements of T
-    static constexpr size_t SMEM = 3 * (size_t)SLOT * sizeof(T);
+    static constexpr int NSLOT = 3;          // planes k-1, k, k+1
+    static constexpr size_t SMEM = NSLOT * (size_t)SLOT * sizeof(T);
     static constexpr int NHALO_PTS = 2 * HW + 2 * TJ;                  // halo points per plane
 };
 
@@ -185,8 +188,9 @@ k_adjoint(const AdjArgs a)
         load_point<T, C>(a, i, j, kk, true, vc);
         if (has_halo) load_point<T, C>(a, hi, hj, kk, false, vh);
     };
+    auto slot_of = [&](int kk) { return ring + (size_t)(((kk % S::NSLOT) + S::NSLOT) % S::NSLOT) * S::SLOT; };
     auto store_plane = [&](int kk) {
-        T *slot = ring + (size_t)(((kk % 3) + 3) % 3) * S::SLOT;
+        T *slot = slot_of(kk);
         store_point<T, TJ>(slot, hc, cpos, vc, is_interior(a, i, j, kk), omega);
         if (has_halo) store_point<T, TJ>(slot, hr * S::HW + hcol, -1, vh, is_interior(a, hi, hj, kk), omega);
     };
@@ -203,9 +207,9 @@ k_adjoint(const AdjArgs a)
         const bool more = (k + 2 <= ke);        // plane k+2 is needed by output k+1
         if (more) load_plane(k + 2);
 
-        const T *Sm = ring + (size_t)(((k - 1) % 3 + 3) % 3) * S::SLOT;
-        const T *Sk = ring + (size_t)((k % 3)) * S::SLOT;
-        const T *Sp = ring + (size_t)(((k + 1) % 3)) * S::SLOT;
+        const T *Sm = slot_of(k - 1);
+        const T *Sk = slot_of(k);
+        const T *Sp = slot_of(k + 1);
         if (mine) {
             auto H = [&](const T *sl, int tile, int pos) { return sl[tile * S::HALO_TILE + pos]; };
             auto Cn = [&](const T *sl, int tile) { return sl[S::NHALO * S::HALO_TILE + tile * S::CEN_TILE + cpos]; };
@@ -249,21 +253,23 @@ k_adjoint(const AdjArgs a)
                 s0 = fma(Cn(Sk, S::CC1), ym, s0);
                 s0 = fma(Cn(Sk, S::CC2), zm, s0);
                 const size_t d = ((size_t)k * a.J + (size_t)j) * (size_t)a.I + (size_t)i;
+                // each sweep's term is formed in T and accumulated in FP64
                 a.g_wrk1[d] += (double)w;
-                a.g_a3[d] = fma((double)mu, (double)s0, a.g_a3[d]);
+                a.g_a3[d] += (double)(mu * s0);
                 if constexpr (CGRAD) {
-                    a.g_coef[0][d] = fma((double)w, (double)xp, a.g_coef[0][d]);
-                    a.g_coef[1][d] = fma((double)w, (double)yp, a.g_coef[1][d]);
-                    a.g_coef[2][d] = fma((double)w, (double)zp, a.g_coef[2][d]);
-                    a.g_coef[3][d] = fma((double)w, (double)bij, a.g_coef[3][d]);
-                    a.g_coef[4][d] = fma((double)w, (double)bjk, a.g_coef[4][d]);
-                    a.g_coef[5][d] = fma((double)w, (double)bik, a.g_coef[5][d]);
-                    a.g_coef[6][d] = fma((double)w, (double)xm, a.g_coef[6][d]);
-                    a.g_coef[7][d] = fma((double)w, (double)ym, a.g_coef[7][d]);
-                    a.g_coef[8][d] = fma((double)w, (double)zm, a.g_coef[8][d]);
+                    a.g_coef[0][d] += (double)(w * xp);
+                    a.g_coef[1][d] += (double)(w * yp);
+                    a.g_coef[2][d] += (double)(w * zp);
+                    a.g_coef[3][d] += (double)(w * bij);
+                    a.g_coef[4][d] += (double)(w * bjk);
+                    a.g_coef[5][d] += (double)(w * bik);
+                    a.g_coef[6][d] += (double)(w * xm);
+                    a.g_coef[7][d] += (double)(w * ym);
+                    a.g_coef[8][d] += (double)(w * zm);
                 }
             }
         }
+        // plane k+2 replaces plane k-1 once every thread is done with it
         __syncthreads();
         if (more) store_plane(k + 2);
         __syncthreads();

@@ -161,9 +161,9 @@ jac::SweepArgs batch_args(const jac_batch *b, int n_iter)
     a.hdr = static_cast<jac::WsHeader *>(b->ws);
     a.partials = reinterpret_cast<double *>(static_cast<char *>(b->ws) + jac::kWsHeaderBytes);
     a.res = b->d_res;
-    size_t state_bytes = 0;
-    for (int g = 0; g < b->n; ++g) state_bytes += 2 * arr_bytes(b, g, JAC_P);
-    a.l2_keep_state = state_bytes <= jac::device_l2_bytes() / 2;
+    size_t points = 0;
+    for (int g = 0; g < b->n; ++g) points += (size_t)jac_pitch(b->I[g]) * b->J[g] * b->K[g];
+    jac::set_l2_policy(a, b->prec, points);
     return a;
 }
 

@@ -26,6 +26,7 @@ jac_status unpack_dev(int I, int J, int K, jac_prec prec, int which, const void 
 jac_status workspace_check(void *workspace, cudaStream_t st);
 int device_sm_count();
 size_t device_l2_bytes();
+void set_l2_policy(SweepArgs &a, jac_prec prec, size_t points);
 int vector_points(jac_prec prec);
 int max_row_fold(jac_prec prec, int tj);
 bool warps_supported(jac_prec prec, int tj);

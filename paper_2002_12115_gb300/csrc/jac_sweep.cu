@@ -128,6 +128,14 @@ const char *thread_last_error() { return g_err.c_str(); }
 void set_thread_error(const std::string &m) { g_err = m; }
 int device_sm_count() { return num_sms(); }
 
+// L2 residency for one launch: keep the state when both buffers fit in half
+// the L2.  `points` = stored points of all grids.
+void set_l2_policy(SweepArgs &a, jac_prec prec, size_t points)
+{
+    const size_t state = 2 * points * (prec == JAC_F64 ? 8 : 4);
+    a.l2_keep_state = state <= device_l2_bytes() / 2;
+}
+
 size_t device_l2_bytes()
 {
     static size_t l2 = 0;
@@ -370,8 +378,7 @@ jac_status sweep_dev(const jac_grid *g, const jac_plan *plan, int n_iter, double
     a.partials = reinterpret_cast<double *>(static_cast<char *>(workspace) + kWsHeaderBytes);
     a.res = d_residual ? d_residual : &hdr->residual;
     a.hdr = hdr;
-    const size_t state_bytes = 2 * (size_t)d0.pitch * g->J * g->K * (g->prec == JAC_F64 ? 8 : 4);
-    a.l2_keep_state = state_bytes <= device_l2_bytes() / 2;
+    set_l2_policy(a, g->prec, (size_t)d0.pitch * g->J * g->K);
     const unsigned nblocks = (unsigned)std::min<long long>(d0.nitems, num_sms());
     return launch_sweep<false>(g->prec, tj, d0, a, nblocks, static_cast<cudaStream_t>(stream));
 }
