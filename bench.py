@@ -157,6 +157,23 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, dist=None, device="cuda") -> float:
+    """The largest of x over all ranks (x itself on one process)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank: float, ms: float, world: int, dist=None, device="cuda") -> tuple:
+    """Whole-job throughput of independent replicas: the units of all ranks
+    over the slowest rank's time.  Returns (value in units/s, max ms)."""
+    ms_max = max_over_ranks(ms, dist, device)
+    return units_per_rank * world / (ms_max * 1e-3), ms_max
+
+
 def events():
     import torch
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -323,7 +340,7 @@ def bench_variant(w, prec, dev, stream, sweeps):
             "gbs": gbs, "grid": [w["I"], w["J"], w["K"]], "prec": prec}
 
 
-def bench_batch(args, stream, sweeps=100, steps=3, autotune=True, loops=True):
+def bench_batch(args, stream, sweeps=100, steps=3, autotune=True, loops=True, tuner="cd"):
     """512 grids, dims drawn from {17, .., 129}: one graph-replayed persistent
     launch per step against loops of per-grid launches."""
     import torch
@@ -338,7 +355,10 @@ def bench_batch(args, stream, sweeps=100, steps=3, autotune=True, loops=True):
     plan = None
     if autotune:
         from paper_2002_12115_gb300 import autotune as at
-        plan = at.tune_batch(b, n_sweeps=10, reps=2, passes=1)
+        if tuner == "ga":
+            plan = at.ga_tune_batch(b, M=10, T=10, n_sweeps=10, reps=2)
+        else:
+            plan = at.tune_batch(b, n_sweeps=10, reps=2, passes=1)
     b.sweep(sweeps)          # capture + warm-up
     b.sweep(sweeps)
     a, e = events()
@@ -425,13 +445,6 @@ def run_native(args, w, wname):
     stream = torch.cuda.current_stream()
     peak, peak_kind = measured_peak()
 
-    def max_over_ranks(x):
-        if args.dist is None:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        args.dist.all_reduce(t, op=args.dist.ReduceOp.MAX)
-        return float(t.item())
-
     def emit(line):
         if rank == 0:
             print(json.dumps(line, default=str), flush=True)
@@ -440,9 +453,9 @@ def run_native(args, w, wname):
             args.dist.destroy_process_group()
 
     if wname == "batch":
-        r = bench_batch(args, stream, sweeps=w["sweeps"], steps=args.steps, autotune=not args.no_autotune)
-        ms = max_over_ranks(r["ms_per_step"])
-        value = r["points"] * r["sweeps"] * world / (ms * 1e-3) / 1e9
+        r = bench_batch(args, stream, sweeps=w["sweeps"], steps=args.steps, autotune=not args.no_autotune,
+                        tuner=args.tuner)
+        value, ms = replica_value(r["points"] * r["sweeps"] / 1e9, r["ms_per_step"], world, args.dist)
         return emit({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                      "warmup": 2, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                      "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -455,7 +468,7 @@ def run_native(args, w, wname):
                      "batch": r, "gpu_launches": args.steps})
     if wname.startswith("adjoint"):
         r = bench_adjoint(args, w, stream, steps=args.steps)
-        ms = max_over_ranks(r["ms_per_pass"])
+        ms = max_over_ranks(r["ms_per_pass"], args.dist)
         return emit({"metric": METRIC + " (adjoint)", "value": r["value"] * world, "unit": UNIT,
                      "n_gpus": world, "steps": args.steps, "warmup": 1, "ms_per_step": ms,
                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[w["prec"]],
@@ -470,11 +483,10 @@ def run_native(args, w, wname):
 
     I, J, K, n, prec = w["I"], w["J"], w["K"], w["sweeps"], w["prec"]
     s = bench_single(args, w, stream)
-    ms = max_over_ranks(s["ms"])
-    value = n_interior(w) * n * args.steps * world / (ms * 1e-3) / 1e9
+    units = n_interior(w) * n * args.steps / 1e9
+    value, ms = replica_value(units, s["ms"], world, args.dist)
     e2e_ms, host = bench_e2e(args, w, s["jac"], stream)
-    e2e_ms = max_over_ranks(e2e_ms)
-    e2e = n_interior(w) * n * args.steps * world / (e2e_ms * 1e-3) / 1e9
+    e2e, e2e_ms = replica_value(units, e2e_ms, world, args.dist)
 
     compare = {}
     if not args.no_variants and rank == 0:
@@ -541,6 +553,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tuner", choices=("cd", "ga"), default="cd",
+                    help="batch plan search: cached coordinate descent or the genetic algorithm")
     ap.add_argument("--quick", action="store_true", help="skip the batched / adjoint / large comparisons")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])

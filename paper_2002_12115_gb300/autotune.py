@@ -181,3 +181,130 @@ def tune_batch(batch, n_sweeps: int = 10, reps: int = 3, passes: int = 2, kdepth
         cache[key] = best_plan
         _store_cache(cache_path, cache)
     return best_plan
+
+
+# --------------------------------------------------------------------------
+# Genetic-algorithm search, after the paper's offload-pattern search
+# (Section 4 and Section 5.1.2): a gene is a bit string; each individual is
+# compiled/run and timed; fitness = (time)^(-1/2), which keeps one fast
+# individual from taking over the population too early; a run that fails
+# (there: did not finish within 3 minutes) counts as a fixed long time
+# (there: 1000 s); roulette-wheel selection with the best individual carried
+# over unchanged (elite preservation); one-point crossover with probability
+# Pc = 0.9 and per-bit mutation with probability Pm = 0.05; the same gene
+# recurs often, so measured patterns are cached.  Here a gene encodes a launch
+# plan instead of which loops to offload.
+
+GA_PC = 0.9
+GA_PM = 0.05
+GA_FAIL_SECONDS = 1000.0
+
+
+class PlanGenome:
+    """Bit layout of a batch launch plan: one bit for the warp count, two bits
+    per I class for the tile width, three bits per K class for the k-depth
+    (values beyond the option list wrap around)."""
+
+    def __init__(self, i_classes, k_classes, widths, kdepths, warps=(8, 4)):
+        self.i_classes, self.k_classes = list(i_classes), list(k_classes)
+        self.widths, self.kdepths, self.warps = list(widths), list(kdepths), list(warps)
+        self.n_bits = 1 + 2 * len(self.i_classes) + 3 * len(self.k_classes)
+
+    @staticmethod
+    def _field(bits, start, n):
+        v = 0
+        for b in bits[start:start + n]:
+            v = (v << 1) | int(b)
+        return v
+
+    def decode(self, bits) -> dict:
+        plan = {"warps": self.warps[self._field(bits, 0, 1) % len(self.warps)], "tile_i": {}, "kdepth": {}}
+        pos = 1
+        for I in self.i_classes:
+            plan["tile_i"][str(I)] = self.widths[self._field(bits, pos, 2) % len(self.widths)]
+            pos += 2
+        for K in self.k_classes:
+            plan["kdepth"][str(K)] = self.kdepths[self._field(bits, pos, 3) % len(self.kdepths)]
+            pos += 3
+        return plan
+
+
+def ga_search(n_bits: int, measure, M: int = 10, T: int = 10, pc: float = GA_PC, pm: float = GA_PM,
+              seed: int = 0, log=None):
+    """Minimise measure(bits) -> seconds (None or inf = failed run) with the
+    paper's GA.  Returns (best_bits, best_time, history); history holds the
+    best time of every generation and the number of distinct measurements."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    cache: dict = {}
+
+    def time_of(bits) -> float:
+        key = tuple(int(b) for b in bits)
+        if key not in cache:
+            t = measure(key)
+            cache[key] = GA_FAIL_SECONDS if (t is None or not np.isfinite(t)) else float(t)
+        return cache[key]
+
+    pop = [tuple(int(b) for b in rng.integers(0, 2, n_bits)) for _ in range(M)]
+    history = []
+    best = None
+    for gen in range(T):
+        times = np.array([time_of(ind) for ind in pop])
+        fit = times ** -0.5
+        order = np.argsort(times)
+        if best is None or times[order[0]] < best[1]:
+            best = (pop[order[0]], float(times[order[0]]))
+        history.append({"generation": gen, "best_s": best[1], "measured": len(cache)})
+        if log:
+            log(f"generation {gen}: best {best[1]:.6f} s, {len(cache)} distinct plans measured")
+        if gen == T - 1:
+            break
+        probs = fit / fit.sum()
+        nxt = [pop[order[0]]]                                      # elite preservation
+        while len(nxt) < M:
+            a, b = (pop[i] for i in rng.choice(M, size=2, p=probs))  # roulette selection
+            a, b = list(a), list(b)
+            if rng.random() < pc and n_bits > 1:                   # one-point crossover
+                cut = int(rng.integers(1, n_bits))
+                a[cut:], b[cut:] = b[cut:], a[cut:]
+            for child in (a, b):
+                for q in range(n_bits):                             # mutation
+                    if rng.random() < pm:
+                        child[q] ^= 1
+                nxt.append(tuple(child))
+                if len(nxt) == M:
+                    break
+        pop = nxt
+    return best[0], best[1], history
+
+
+def ga_tune_batch(batch, M: int = 10, T: int = 10, n_sweeps: int = 10, reps: int = 2, seed: int = 0,
+                  kdepths=(4, 8, 16, 32, 64, 12, 24, 48), warps=(8, 4), log=None) -> dict:
+    """Per-size-class plan of a JacobiBatch by the GA above, each individual
+    timed on the GPU.  Returns the best plan with the search history."""
+    dims = batch.dims
+    genome = PlanGenome(sorted({d[0] for d in dims}), sorted({d[2] for d in dims}),
+                        _tile_widths(batch.prec), kdepths, warps)
+
+    def expand(plan):
+        ti = [plan["tile_i"][str(I)] for I, _, _ in dims]
+        kd = [min(plan["kdepth"][str(K)], max(K - 2, 1)) for _, _, K in dims]
+        return ti, kd
+
+    def measure(bits):
+        plan = genome.decode(bits)
+        ti, kd = expand(plan)
+        try:
+            batch.set_plan(plan["warps"], ti, kd)
+            batch.sweep(n_sweeps, residuals=False)
+        except JacError:
+            return None
+        return time_call(lambda: batch.sweep(n_sweeps, residuals=False), reps)
+
+    bits, t, history = ga_search(genome.n_bits, measure, M=M, T=T, seed=seed, log=log)
+    plan = genome.decode(bits)
+    ti, kd = expand(plan)
+    batch.set_plan(plan["warps"], ti, kd)
+    plan["s_per_sweep"] = t / n_sweeps
+    plan["history"] = history
+    return plan
