@@ -259,14 +259,19 @@ jac_status jac_get_grid(const jac_ctx *ctx, jac_grid *g);
 
 /* One adjoint sweep, stateless.  g describes the grid (coefficients; p[0]
  * and p[1] unused).  p_t: the state before the sweep, lam_in: lambda_{t+1},
- * lam_out: lambda_t (storage layout, element type of p; lam_out != lam_in;
- * every point including faces is written).  g_wrk1, g_a3: dense FP64
- * (I*J*K) arrays, accumulated (+=).  g_coef: NULL, or nine dense FP64
- * arrays for a0, a1, a2, b0, b1, b2, c0, c1, c2, accumulated.  kdepth: planes
- * per CTA (0: 16).  Asynchronous on stream. */
+ * lam_out: lambda_t (storage layout, element type of p, 16-byte aligned;
+ * lam_out != lam_in; every point including faces is written, the row
+ * padding may be written too).  g_wrk1, g_a3: dense FP64 (I*J*K) arrays,
+ * accumulated (+=).  g_coef: NULL, or nine dense FP64 arrays for a0, a1, a2,
+ * b0, b1, b2, c0, c1, c2, accumulated.  kdepth: output planes per work item
+ * (0: chosen from the grid).  workspace: at least 256 bytes, 256-byte
+ * aligned (a sweep workspace serves); a device wait that gives up sets its
+ * error word, which jac_workspace_check reports as JAC_ETIMEOUT.
+ * Asynchronous on stream; coefficient arrays must be finite on the faces
+ * too (a face's w is 0, and 0 * coefficient must be 0). */
 jac_status jac_adjoint_step_dev(const jac_grid *g, const void *p_t, const void *lam_in, void *lam_out,
                                 double *g_wrk1, double *g_a3, double *const *g_coef, int kdepth,
-                                void *stream);
+                                void *workspace, size_t ws_bytes, void *stream);
 
 /* Start a checkpoint tape: the next sweeps (at most max_sweeps, across any
  * number of jac_sweep calls) are recorded by saving the state at the start

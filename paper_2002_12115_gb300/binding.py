@@ -72,7 +72,7 @@ _SIG = {
     "jac_sweep_count": (_I, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
     "jac_get_grid": (_I, [_VP, ctypes.POINTER(jac_grid)]),
     "jac_sweep_unhoisted": (_I, [_VP, _I, ctypes.POINTER(jac_fields), _VP]),
-    "jac_adjoint_step_dev": (_I, [ctypes.POINTER(jac_grid), _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP]),
+    "jac_adjoint_step_dev": (_I, [ctypes.POINTER(jac_grid), _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP, ctypes.c_size_t, _VP]),
     "jac_tape_begin": (_I, [_VP, _I, _I]),
     "jac_tape_end": (_I, [_VP]),
     "jac_tape_count": (_I, [_VP, ctypes.POINTER(_I)]),
@@ -294,6 +294,30 @@ def sweep_dev(grid: jac_grid, n: int, d_residual: int | None, workspace: int, ws
     check(lib().jac_sweep_dev(ctypes.byref(grid), ctypes.byref(jac_plan(tile_j, kdepth, tile_i)), int(n),
                               _VP(d_residual) if d_residual else None, _VP(workspace), ctypes.c_size_t(ws_bytes),
                               _VP(stream)))
+
+
+def workspace_check(workspace: int, stream: int) -> None:
+    """Synchronise the stream and raise if a kernel set the workspace error word."""
+    check(lib().jac_workspace_check(_VP(workspace), _VP(stream)))
+
+
+def pack_dev(I: int, J: int, K: int, prec: str, which: int, src: int, dst: int, stream: int) -> None:
+    """Dense FP64 device array -> storage layout of array `which` (index into FIELDS)."""
+    check(lib().jac_pack_dev(int(I), int(J), int(K), PRECS[prec], int(which), _VP(src), _VP(dst), _VP(stream)))
+
+
+def unpack_dev(I: int, J: int, K: int, prec: str, which: int, src: int, dst: int, stream: int) -> None:
+    """Storage layout of array `which` -> dense FP64 device array."""
+    check(lib().jac_unpack_dev(int(I), int(J), int(K), PRECS[prec], int(which), _VP(src), _VP(dst), _VP(stream)))
+
+
+def adjoint_step_dev(grid: jac_grid, p_t: int, lam_in: int, lam_out: int, g_wrk1: int, g_a3: int,
+                     workspace: int, ws_bytes: int, stream: int, g_coef=None, kdepth: int = 0) -> None:
+    """The stateless entry point jac_adjoint_step_dev (device pointers)."""
+    gc = (_VP * 9)(*g_coef) if g_coef is not None else None
+    check(lib().jac_adjoint_step_dev(ctypes.byref(grid), _VP(p_t), _VP(lam_in), _VP(lam_out), _VP(g_wrk1),
+                                     _VP(g_a3), gc, int(kdepth), _VP(workspace), ctypes.c_size_t(ws_bytes),
+                                     _VP(stream)))
 
 
 class JacobiBatch:

@@ -388,7 +388,8 @@ jac_status jac_sweep_adjoint(jac_ctx *c, const double *lam_T, double *g_wrk1, do
             if (s != JAC_OK) return ctx_from_thread(c, s);
         }
         for (int m = len - 1; m >= 0; --m) {     // reverse sweeps of the segment
-            s = jac::adjoint_step_dev(&g, tp.seg(m), tp.lam(lc), tp.lam(lc ^ 1), g_wrk1, g_a3, g_coef, 0, c->stream);
+            s = jac::adjoint_step_dev(&g, tp.seg(m), tp.lam(lc), tp.lam(lc ^ 1), g_wrk1, g_a3, g_coef, 0, c->ws,
+                                      c->ws_bytes, c->stream);
             if (s != JAC_OK) return ctx_from_thread(c, s);
             lc ^= 1;
         }

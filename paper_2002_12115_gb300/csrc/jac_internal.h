@@ -1,6 +1,7 @@
 // Internal interfaces shared by the translation units of libjac.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <string>
@@ -37,6 +38,12 @@ template <bool BATCH>
 jac_status launch_sweep(jac_prec prec, int tj, const GridDesc &d0, const SweepArgs &a, unsigned nblocks,
                         cudaStream_t st);
 jac_status adjoint_step_dev(const jac_grid *g, const void *p_t, const void *lam_in, void *lam_out, double *g_wrk1,
-                            double *g_a3, double *const *g_coef, int kdepth, cudaStream_t st);
+                            double *g_a3, double *const *g_coef, int kdepth, void *workspace, size_t ws_bytes,
+                            cudaStream_t st);
+// 3-D tensor map of one storage-layout array (row pitch `pitch` elements)
+// with extent (extent_i, J, K), so that columns at i >= extent_i read as
+// zero, and a (bx, by, 1) box.
+jac_status encode_box_map(CUtensorMap *m, const void *base, size_t elem, int extent_i, int pitch, int J, int K,
+                          int bx, int by);
 
 }  // namespace jac

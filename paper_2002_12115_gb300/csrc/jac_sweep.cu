@@ -124,6 +124,22 @@ int num_sms()
 
 }  // namespace
 
+jac_status encode_box_map(CUtensorMap *m, const void *base, size_t elem, int extent_i, int pitch, int J, int K,
+                          int bx, int by)
+{
+    jac_status s = ensure_encode();
+    if (s != JAC_OK) return s;
+    const cuuint64_t dims[3] = {(cuuint64_t)extent_i, (cuuint64_t)J, (cuuint64_t)K};
+    const cuuint64_t strides[2] = {(cuuint64_t)pitch * elem, (cuuint64_t)pitch * J * elem};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    CUresult r = g_encode(m, map_type(elem), 3, const_cast<void *>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(JAC_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return JAC_OK;
+}
+
 const char *thread_last_error() { return g_err.c_str(); }
 void set_thread_error(const std::string &m) { g_err = m; }
 int device_sm_count() { return num_sms(); }
