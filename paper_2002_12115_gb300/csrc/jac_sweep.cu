@@ -144,12 +144,33 @@ const char *thread_last_error() { return g_err.c_str(); }
 void set_thread_error(const std::string &m) { g_err = m; }
 int device_sm_count() { return num_sms(); }
 
+// Share of the L2 that the state and the coefficient arrays kept with it
+// may claim together.  Measured on GB300 (129 x 129 x 257): 0.6 keeps the
+// state and two FP32 arrays (72 MB) and gains 2-3% over the state alone;
+// 90 MB and more of evict_last lines thrash and lose up to 15%.
+constexpr double kL2KeepFraction = 0.6;
+
 // L2 residency for one launch: keep the state when both buffers fit in half
-// the L2.  `points` = stored points of all grids.
+// the L2; then keep whole coefficient arrays, in a fixed order, while state
+// and kept arrays together stay within kL2KeepFraction of the L2.  `points` =
+// stored points of all grids.
 void set_l2_policy(SweepArgs &a, jac_prec prec, size_t points)
 {
+    const size_t l2 = device_l2_bytes();
     const size_t state = 2 * points * (prec == JAC_F64 ? 8 : 4);
-    a.l2_keep_state = state <= device_l2_bytes() / 2;
+    a.l2_keep_state = state <= l2 / 2;
+    a.l2_keep_coef = 0;
+    if (!a.l2_keep_state) return;
+    const double budget = kL2KeepFraction * (double)l2;
+    static const int order[12] = {JAC_WRK1, JAC_A3, JAC_BND, JAC_A0, JAC_A1, JAC_A2,
+                                  JAC_C0,   JAC_C1, JAC_C2,  JAC_B0, JAC_B1, JAC_B2};
+    double used = (double)state;
+    for (int q : order) {
+        const double bytes = (double)points * (double)elem_bytes(prec, q);
+        if (used + bytes > budget) break;
+        used += bytes;
+        a.l2_keep_coef |= 1u << q;
+    }
 }
 
 size_t device_l2_bytes()

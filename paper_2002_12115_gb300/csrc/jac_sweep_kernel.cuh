@@ -35,7 +35,10 @@
 //   * when both state buffers fit in half the L2 (129 MB on GB300), the state
 //     copies and stores carry an evict_last policy and the coefficient copies
 //     evict_first: the state then stays L2-resident from one sweep to the
-//     next and only the coefficients stream from HBM;
+//     next and only the coefficients stream from HBM.  Whole coefficient
+//     arrays that still fit a resident budget beside the state are marked
+//     evict_last as well (l2_keep_coef), so that they too are read from L2
+//     on every sweep after the first;
 //   * every wait is bounded; on expiry the kernel sets the workspace error
 //     word, drains its own copies and returns.
 #pragma once
@@ -66,6 +69,7 @@ struct SweepArgs {
     double *res;               // residual of the last sweep per grid (NULL: none)
     WsHeader *hdr;
     int l2_keep_state;         // 1: state copies/stores evict_last, coefficients evict_first
+    unsigned l2_keep_coef;     // bit q (JAC_A0..JAC_BND): array q's copies evict_last too
 };
 
 // Fast2Sum step (Dekker): hi + b = s + err exactly when |hi| >= |b|.
@@ -264,6 +268,7 @@ k_sweep(const __grid_constant__ GridDesc d0, const SweepArgs a)
         // -------------------------------------------- coefficient producer
         if (lane == 0) {
             const uint64_t pol = l2_policy(a.l2_keep_state ? -1 : 0);
+            const uint64_t pol_keep = l2_policy(1);
             uint32_t cc = 0;
             bool ok = true;
             for (int t = 0; t < n_iter && ok; ++t)
@@ -277,7 +282,7 @@ k_sweep(const __grid_constant__ GridDesc d0, const SweepArgs a)
                         mbar_arrive_expect_tx(&c_full[slot], S::C_TX);
                         for (int q = JAC_A0; q <= JAC_BND; ++q)
                             tma_load_3d_hint(st + S::tile_off(q), &it.D->coef[q - 1], &c_full[slot], it.i0,
-                                             it.j0, it.kb + m, pol);
+                                             it.j0, it.kb + m, ((a.l2_keep_coef >> q) & 1u) ? pol_keep : pol);
                     }
                 }
             if (!ok) {

@@ -299,7 +299,9 @@ def test_adjoint_matches_central_differences(oracle_mod):
     the forward oracle.  L is quadratic in wrk1 (the sweeps are affine in it),
     so the wrk1 check is exact up to rounding; a3 and the other coefficients
     enter polynomially.  h = 1e-6; the bar allows the rounding error of a
-    central difference, about eps * L / h, on top of 1e-6 max|g| + 1e-5 |g|."""
+    central difference, about eps * L / h, on top of 1e-6 max|g| + 1e-5 |g|.
+    L is quadratic in p0 as well (the sweeps are affine in the state), so
+    that check is exact up to rounding too."""
     I, J, K, T = 9, 10, 11, 6
     f = ji.himeno_fields(I, J, K, seed=30)
     target = ji.target_field(I, J, K)
@@ -310,8 +312,15 @@ def test_adjoint_matches_central_differences(oracle_mod):
     pw, pa = ji.fd_points(I, J, K, 8)
     h = 1e-6
     gmax = {}
-    for name, pts in (("wrk1", pw), ("a3", pa), ("a0", pw), ("b1", pa), ("c2", pw), ("b2", pw)):
-        g = adj["g_" + name]
+    # every parameter the adjoint differentiates: wrk1, a3, the nine stencil
+    # coefficients and the initial state p0 (faces of p0 included: they are
+    # read by the first sweep)
+    names = ("wrk1", "a3", "a0", "a1", "a2", "b0", "b1", "b2", "c0", "c1", "c2", "p")
+    for q, name in enumerate(names):
+        g = adj["g_p0" if name == "p" else "g_" + name]
+        pts = (pw, pa)[q % 2]
+        if name == "p":
+            pts = list(pts) + [(0, 4, 5), (3, 0, 2), (I - 1, 5, 7)]
         for (i, j, k) in pts:
             fp = {n: v.copy() for n, v in f.items()}
             fm = {n: v.copy() for n, v in f.items()}
