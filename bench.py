@@ -85,6 +85,43 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
+# FP64 operations (DADD, DMUL, DFMA, each one issue of the FP64 pipe) per
+# interior point of a non-residual FP64 sweep: 9 in the three b-brackets, 9
+# fused terms of s0, one fused and one plain product for ss, one fused update.
+F64_OPS_PER_POINT = 21
+# GB300 issues two FP64 thread operations per SM per clock (the ncu peak of
+# sm__sass_thread_inst_executed_op_dfma_pred_on is 2 per SM per cycle).
+F64_OPS_PER_SM_CLK = 2
+GB300_SMS = 152
+
+
+def f64_alu_peak_gops():
+    """FP64 ALU ceiling in G FP64 operations/s: 2 per SM per clock x 152 SMs x
+    the maximum SM clock from MEASURED_PEAKS.json (2070 MHz if absent)."""
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            mhz = float(json.load(fh).get("sm_max_mhz", mhz))
+    except Exception:
+        pass
+    return F64_OPS_PER_SM_CLK * GB300_SMS * mhz * 1e6 / 1e9
+
+
+def variant_roofline(prec: str, gpts: float) -> dict:
+    """Roofline of one sweep variant: HBM for FP32 and BF16 storage, the FP64
+    ALU for FP64 (its 112 B per point would need more than the HBM peak only
+    above 61 Gpoint-updates/s; the FP64 pipe caps it near 30)."""
+    if prec == "f64":
+        ach = F64_OPS_PER_POINT * gpts
+        peak = f64_alu_peak_gops()
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "G FP64 op/s", "frac": ach / peak,
+                "peak_kind": "derived: 2 FP64 ops per SM per clock x 152 SMs x max SM clock",
+                "ops_per_point": F64_OPS_PER_POINT}
+    peak, kind = measured_peak()
+    ach = BYTES_PER_POINT[prec] * gpts
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "peak_kind": kind}
+
+
 def kernel_source_hash(names=("jac_sweep_kernel.cuh", "jac_common.cuh")) -> str:
     h = hashlib.sha256()
     for name in names:
@@ -336,8 +373,9 @@ def bench_variant(w, prec, dev, stream, sweeps):
         vj.residual()
         ms = a.elapsed_time(b)
     gbs = BYTES_PER_POINT[prec] * n_interior(w) / (ms / sweeps * 1e-3) / 1e9
-    return {"value": n_interior(w) * sweeps / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_sweep": ms / sweeps,
-            "gbs": gbs, "grid": [w["I"], w["J"], w["K"]], "prec": prec}
+    gpts = n_interior(w) * sweeps / (ms * 1e-3) / 1e9
+    return {"value": gpts, "unit": UNIT, "ms_per_sweep": ms / sweeps,
+            "gbs": gbs, "grid": [w["I"], w["J"], w["K"]], "prec": prec, "roofline": variant_roofline(prec, gpts)}
 
 
 def bench_batch(args, stream, sweeps=100, steps=3, autotune=True, loops=True, tuner="cd"):
@@ -510,6 +548,14 @@ def run_native(args, w, wname):
     bytes_launch = BYTES_PER_POINT[prec] * n_interior(w) * n
     achieved = bytes_launch / (s["launch_ms"] * 1e-3) / 1e9
     per_sweep = profiled_traffic(f"{I}x{J}x{K} {prec}")
+    if prec == "f64":
+        roofline = variant_roofline("f64", n_interior(w) * n / (s["launch_ms"] * 1e-3) / 1e9)
+    else:
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "peak_kind": peak_kind}
+    roofline.update({"traffic": per_sweep * n if per_sweep else None, "kernel": "k_sweep",
+                     "algorithmic_bytes_per_launch": bytes_launch, "launch_ms": s["launch_ms"],
+                     "sweeps_per_launch": n})
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         gpts, cores, sample = oracle_sample(w, min_seconds=args.cpu_seconds)
@@ -523,11 +569,7 @@ def run_native(args, w, wname):
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "step": "device-side copy-in of resident FP64 inputs, sweeps (one persistent launch), "
                            "residual, copy-out"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": peak_kind,
-                     "traffic": per_sweep * n if per_sweep else None, "kernel": "k_sweep",
-                     "algorithmic_bytes_per_launch": bytes_launch, "launch_ms": s["launch_ms"],
-                     "sweeps_per_launch": n},
+        "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 13 * I * J * K * 8,
                 "d2h_bytes_per_step": I * J * K * 8 + 8},

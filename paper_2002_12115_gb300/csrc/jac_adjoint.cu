@@ -53,10 +53,11 @@
 namespace jac {
 
 // Stage geometry of one kernel instantiation: element type T of p, lambda
-// and wrk1, coefficient storage C, TJ consumer warps (rows per tile).
-template <typename T, typename C, int TJ>
+// and wrk1, coefficient storage C, TJ consumer warps (rows per tile), VI
+// points per lane.
+template <typename T, typename C, int TJ, int VI_>
 struct AdjGeom {
-    static constexpr int VI = 16 / (int)sizeof(T);      // points per lane
+    static constexpr int VI = VI_;                       // points per lane
     static constexpr int TI = 32 * VI;                   // tile width
     static constexpr int HT = 16 / (int)sizeof(T);       // halo columns of a T array (16 bytes)
     static constexpr int HC = 16 / (int)sizeof(C);       // halo columns of a C array
@@ -134,14 +135,63 @@ __device__ __forceinline__ AdjItem adj_item(const AdjDesc &d, int item)
     return it;
 }
 
+// VI consecutive values of T from shared memory (16- or 8-byte aligned).
+template <typename T, int VI>
+__device__ __forceinline__ void adj_lds(const T *p, T (&v)[VI])
+{
+    if constexpr (sizeof(T) * VI == 16) {
+        lds_vec<T, VI>(p, v);
+    } else if constexpr (sizeof(T) == 4 && VI == 2) {
+        const float2 x = *reinterpret_cast<const float2 *>(p);
+        v[0] = x.x; v[1] = x.y;
+    } else {
+        static_assert(sizeof(T) == 8 && VI == 1, "unsupported vector shape");
+        v[0] = *p;
+    }
+}
+
+// VI BF16 values from shared memory as FP32 (exact: the BF16 bits are the
+// high half of the FP32 word), or VI values of T.
+template <typename T, typename C, int VI>
+__device__ __forceinline__ void adj_coef(const unsigned char *tile, int idx, T (&o)[VI])
+{
+    if constexpr (sizeof(C) == 2 && VI == 2) {
+        const uint32_t v = *reinterpret_cast<const uint32_t *>(tile + (size_t)idx * 2);
+        o[0] = __uint_as_float(v << 16);
+        o[1] = __uint_as_float(v & 0xffff0000u);
+    } else if constexpr (sizeof(C) == 2) {
+        smem_coef<T, C, VI>(tile, idx, o);
+    } else {
+        adj_lds<T, VI>(reinterpret_cast<const T *>(tile) + idx, o);
+    }
+}
+
+// VI values of a state row plus the left and right neighbours: lane
+// shuffles inside the warp, the halo columns for lanes 0 and 31.
+template <typename T, int VI, int H>
+__device__ __forceinline__ void adj_load_ext(const T *row, int lane, T (&e)[VI + 2])
+{
+    const int col = H + VI * lane;
+    T v[VI];
+    adj_lds<T, VI>(row + col, v);
+#pragma unroll
+    for (int q = 0; q < VI; ++q) e[q + 1] = v[q];
+    T l = __shfl_up_sync(0xffffffffu, e[VI], 1);
+    T r = __shfl_down_sync(0xffffffffu, e[1], 1);
+    if (lane == 0) l = row[col - 1];
+    if (lane == 31) r = row[col + VI];
+    e[0] = l;
+    e[VI + 1] = r;
+}
+
 // VI values of stage array Q at tile row `row` (-up .. TJ-1+dn) and tile
 // column `col` (a multiple of VI), as T.
 template <typename G, int Q, typename T, int VI>
 __device__ __forceinline__ void st_vec(const unsigned char *st, int row, int col, T (&o)[VI])
 {
     const int idx = (row + G::up(Q)) * G::width(Q) + col + G::hl(Q);
-    if constexpr (G::esz(Q) == (int)sizeof(T)) lds_vec<T, VI>(reinterpret_cast<const T *>(st + G::off(Q)) + idx, o);
-    else smem_coef<T, __nv_bfloat16, VI>(st + G::off(Q), idx, o);
+    if constexpr (G::esz(Q) == (int)sizeof(T)) adj_lds<T, VI>(reinterpret_cast<const T *>(st + G::off(Q)) + idx, o);
+    else adj_coef<T, __nv_bfloat16, VI>(st + G::off(Q), idx, o);
 }
 
 // One value of stage array Q (col may be -1 or TI, the halo columns), as T.
@@ -160,15 +210,17 @@ __device__ __forceinline__ T st_one(const unsigned char *st, int row, int col)
 template <typename T, int VI>
 __device__ __forceinline__ void stg_vec(T *p, const T (&v)[VI])
 {
-    if constexpr (sizeof(T) == 4) *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-    else *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+    if constexpr (sizeof(T) == 4 && VI == 4) *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    else if constexpr (sizeof(T) == 4 && VI == 2) *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+    else if constexpr (VI == 2) *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+    else *p = v[0];
 }
 
-template <typename T, typename C, int TJ, bool CGRAD>
-__global__ void __launch_bounds__(AdjGeom<T, C, TJ>::THREADS, 1)
+template <typename T, typename C, int TJ, int VI_, bool CGRAD>
+__global__ void __launch_bounds__(AdjGeom<T, C, TJ, VI_>::THREADS, 1)
 k_adjoint(const __grid_constant__ AdjDesc d)
 {
-    using G = AdjGeom<T, C, TJ>;
+    using G = AdjGeom<T, C, TJ, VI_>;
     constexpr int VI = G::VI, TI = G::TI, HT = G::HT, RP = G::RP, RC = G::RC;
     extern __shared__ unsigned char adj_raw[];
     unsigned char *base =
@@ -446,15 +498,15 @@ k_adjoint(const __grid_constant__ AdjDesc d)
                     const int r0 = r * W, r1 = (r + 1) * W, r2 = (r + 2) * W;   // rows j-1, j, j+1
                     T ek0[VI + 2], ek1[VI + 2], ek2[VI + 2], em1[VI + 2], ep1[VI + 2];
                     T vm0[VI], vm2[VI], vp0[VI], vp2[VI];
-                    load_ext<T, VI, HT>(Pk + r0, lane, 32, ek0);
-                    load_ext<T, VI, HT>(Pk + r1, lane, 32, ek1);
-                    load_ext<T, VI, HT>(Pk + r2, lane, 32, ek2);
-                    load_ext<T, VI, HT>(Pm + r1, lane, 32, em1);
-                    load_ext<T, VI, HT>(Pp + r1, lane, 32, ep1);
-                    lds_vec<T, VI>(Pm + r0 + HT + VI * lane, vm0);
-                    lds_vec<T, VI>(Pm + r2 + HT + VI * lane, vm2);
-                    lds_vec<T, VI>(Pp + r0 + HT + VI * lane, vp0);
-                    lds_vec<T, VI>(Pp + r2 + HT + VI * lane, vp2);
+                    adj_load_ext<T, VI, HT>(Pk + r0, lane, ek0);
+                    adj_load_ext<T, VI, HT>(Pk + r1, lane, ek1);
+                    adj_load_ext<T, VI, HT>(Pk + r2, lane, ek2);
+                    adj_load_ext<T, VI, HT>(Pm + r1, lane, em1);
+                    adj_load_ext<T, VI, HT>(Pp + r1, lane, ep1);
+                    adj_lds<T, VI>(Pm + r0 + HT + VI * lane, vm0);
+                    adj_lds<T, VI>(Pm + r2 + HT + VI * lane, vm2);
+                    adj_lds<T, VI>(Pp + r0 + HT + VI * lane, vp0);
+                    adj_lds<T, VI>(Pp + r2 + HT + VI * lane, vp2);
                     T a1c[VI], a2c[VI], b0c[VI], b1c[VI], b2c[VI], c1c[VI], c2c[VI], wk[VI];
                     st_vec<G, G::A1, T, VI>(st, r, VI * lane, a1c);
                     st_vec<G, G::A2, T, VI>(st, r, VI * lane, a2c);
@@ -533,25 +585,29 @@ jac_status adj_fail(jac_status s, const std::string &m)
     return s;
 }
 
-template <typename T, typename C, int TJ, bool CGRAD>
+template <typename T, typename C, int TJ, int VI, bool CGRAD>
 jac_status launch_adj(const AdjDesc &d, unsigned nblocks, cudaStream_t st)
 {
-    using G = AdjGeom<T, C, TJ>;
+    using G = AdjGeom<T, C, TJ, VI>;
     static_assert(G::RC >= 2, "stage ring too shallow for the shared-memory budget");
     static std::once_flag once;
     static cudaError_t err = cudaSuccess;
     std::call_once(once, [] {
-        err = cudaFuncSetAttribute(k_adjoint<T, C, TJ, CGRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        err = cudaFuncSetAttribute(k_adjoint<T, C, TJ, VI, CGRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)G::SMEM);
     });
     if (err != cudaSuccess) return adj_fail(JAC_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(err));
-    k_adjoint<T, C, TJ, CGRAD><<<nblocks, G::THREADS, G::SMEM, st>>>(d);
+    k_adjoint<T, C, TJ, VI, CGRAD><<<nblocks, G::THREADS, G::SMEM, st>>>(d);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return adj_fail(JAC_ECUDA, std::string("adjoint launch: ") + cudaGetErrorString(e));
     return JAC_OK;
 }
 
-constexpr int kAdjRows = 8;   // consumer warps = tile rows
+
+// Launch shapes: consumer warps (tile rows) and points per lane.  FP32
+// state: 16 rows of 64 points (two per lane), twice the warps of an 8 x 128
+// tile for the same shared memory; FP64: 8 rows of 64 points.
+constexpr int kAdjRowsF32 = 16, kAdjVIF32 = 2, kAdjRowsF64 = 8;
 
 // Output planes per item: 32, fewer while the grid has too few items to give
 // every SM two.
@@ -562,17 +618,18 @@ int adj_kdepth(int K, long long tiles_ij, int sms)
     return kd;
 }
 
-template <typename T, typename C>
+// TJ consumer warps (tile rows) of VI points per lane.
+template <typename T, typename C, int TJ, int VI>
 jac_status run_adj(const jac_grid *g, const void *p_t, const void *lam_in, void *lam_out, double *g_wrk1,
                    double *g_a3, double *const *g_coef, int kdepth, WsHeader *hdr, cudaStream_t st)
 {
-    using G = AdjGeom<T, C, kAdjRows>;
+    using G = AdjGeom<T, C, TJ, VI>;
     AdjDesc d;
     std::memset(&d, 0, sizeof(d));
     d.I = g->I; d.J = g->J; d.K = g->K;
     d.pitch = jac_pitch(g->I);
     d.nti = std::max(1, (g->I - 1 + G::TI - 1) / G::TI);   // column I-1 may be a tile's extra column
-    d.ntj = (g->J + kAdjRows - 1) / kAdjRows;
+    d.ntj = (g->J + TJ - 1) / TJ;
     const int sms = device_sm_count();
     d.kdepth = kdepth > 0 ? kdepth : adj_kdepth(g->K, (long long)d.nti * d.ntj, sms);
     const long long items = (long long)d.nti * d.ntj * ((g->K + d.kdepth - 1) / d.kdepth);
@@ -604,7 +661,7 @@ jac_status run_adj(const jac_grid *g, const void *p_t, const void *lam_in, void 
     }
     if ((s = encode_box_map(&d.pmap, p_t, sizeof(T), g->I, d.pitch, g->J, g->K, G::PW, G::PH)) != JAC_OK) return s;
     const unsigned nblocks = (unsigned)std::min<long long>(items, sms);
-    return cgrad ? launch_adj<T, C, kAdjRows, true>(d, nblocks, st) : launch_adj<T, C, kAdjRows, false>(d, nblocks, st);
+    return cgrad ? launch_adj<T, C, TJ, VI, true>(d, nblocks, st) : launch_adj<T, C, TJ, VI, false>(d, nblocks, st);
 }
 
 }  // namespace
@@ -625,10 +682,15 @@ jac_status adjoint_step_dev(const jac_grid *g, const void *p_t, const void *lam_
     if (kdepth < 0) return adj_fail(JAC_EINVAL, "adjoint: kdepth must be >= 0");
     WsHeader *hdr = static_cast<WsHeader *>(workspace);
     switch (g->prec) {
-    case JAC_F64: return run_adj<double, double>(g, p_t, lam_in, lam_out, g_wrk1, g_a3, g_coef, kdepth, hdr, st);
-    case JAC_F32: return run_adj<float, float>(g, p_t, lam_in, lam_out, g_wrk1, g_a3, g_coef, kdepth, hdr, st);
+    case JAC_F64:
+        return run_adj<double, double, kAdjRowsF64, 2>(g, p_t, lam_in, lam_out, g_wrk1, g_a3, g_coef, kdepth, hdr,
+                                                        st);
+    case JAC_F32:
+        return run_adj<float, float, kAdjRowsF32, kAdjVIF32>(g, p_t, lam_in, lam_out, g_wrk1, g_a3, g_coef, kdepth,
+                                                             hdr, st);
     case JAC_F32_BF16COEF:
-        return run_adj<float, __nv_bfloat16>(g, p_t, lam_in, lam_out, g_wrk1, g_a3, g_coef, kdepth, hdr, st);
+        return run_adj<float, __nv_bfloat16, kAdjRowsF32, kAdjVIF32>(g, p_t, lam_in, lam_out, g_wrk1, g_a3, g_coef,
+                                                                     kdepth, hdr, st);
     }
     return adj_fail(JAC_EINVAL, "unknown precision");
 }
