@@ -116,8 +116,8 @@ typedef struct jac_grid {
  * two in [16, 128] (FP64: [16, 64]); W must be 4 or 8, or 16 with BF16
  * coefficients and tile_i >= 32.  Zero fields pick defaults: W = 8 (16 for
  * BF16 on grids a 128-wide tile covers fully), the tile width with the best
- * lane use, and kdepth for about 12 work items per SM.  Unsupported shapes:
- * JAC_EINVAL at launch. */
+ * lane use, and the kdepth that minimises (work-item rounds per CTA) x
+ * (kdepth + 3).  Unsupported shapes: JAC_EINVAL at launch. */
 typedef struct jac_plan {
     int tile_j;   /* rows per work item */
     int kdepth;   /* k-planes per work item, >= 1 */

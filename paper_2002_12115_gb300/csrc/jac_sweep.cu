@@ -216,10 +216,31 @@ int best_tile_i(int I, int J, jac_prec prec, int tj)
     return best;
 }
 
+// k-planes per work item when the plan leaves it open.  A CTA walks its
+// items one after another, so a sweep takes about rounds x (kdepth + h)
+// plane-times, rounds = ceil(items / CTAs), where h = 3 stands for the two
+// extra state planes of an item and the refill of its rings.  Deep items cut
+// that overhead; shallow ones balance the CTAs.  The smallest such cost wins
+// (ties: the deeper item).
+int default_kdepth(long cols, int nk, int ctas)
+{
+    if (nk <= 1) return 1;
+    const long h = 3;
+    int best = 2;
+    long best_cost = -1;
+    for (int kd = 2; kd <= std::min(nk, 256); ++kd) {
+        const long items = cols * ((nk + kd - 1) / kd);
+        const long rounds = (items + ctas - 1) / ctas;
+        const long cost = rounds * (kd + h);
+        if (best_cost < 0 || cost <= best_cost) { best_cost = cost; best = kd; }
+    }
+    return best;
+}
+
 jac_plan resolve_plan(const jac_grid *g, const jac_plan *plan)
 {
     // defaults: 8 consumer warps (16 for BF16 coefficients on wide grids),
-    // the tile width with the best lane use, about 12 work items per SM
+    // the tile width with the best lane use, kdepth from default_kdepth
     const int vi = vector_points(g->prec), full = 32 * vi;
     int tj = 8;
     jac_plan p;
@@ -244,11 +265,7 @@ jac_plan resolve_plan(const jac_grid *g, const jac_plan *plan)
     if (p.kdepth == 0) {
         const int ti = std::max(p.tile_i, 1), rows = std::max(p.tile_j, 1);
         const long cols = (long)((g->I - 2) / ti + 1) * ((g->J - 2 + rows - 1) / rows);
-        const long target = 12L * num_sms();
-        long kd = (cols * (g->K - 2) + target - 1) / target;
-        if (kd < 2) kd = 2;
-        if (kd > g->K - 2) kd = g->K - 2;
-        p.kdepth = (int)kd;
+        p.kdepth = default_kdepth(cols, g->K - 2, num_sms());
     }
     return p;
 }
