@@ -556,6 +556,11 @@ def run_native(args, w, wname):
     roofline.update({"traffic": per_sweep * n if per_sweep else None, "kernel": "k_sweep",
                      "algorithmic_bytes_per_launch": bytes_launch, "launch_ms": s["launch_ms"],
                      "sweeps_per_launch": n})
+    if per_sweep:
+        # DRAM bandwidth actually drawn: the ncu bytes per sweep over the live
+        # launch time.  Below the algorithmic figure when arrays stay in L2.
+        dram = per_sweep * n / (s["launch_ms"] * 1e-3) / 1e9
+        roofline.update({"dram_achieved": dram, "dram_frac": dram / peak})
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         gpts, cores, sample = oracle_sample(w, min_seconds=args.cpu_seconds)

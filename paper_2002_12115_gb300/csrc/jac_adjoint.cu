@@ -605,9 +605,11 @@ jac_status launch_adj(const AdjDesc &d, unsigned nblocks, cudaStream_t st)
 
 
 // Launch shapes: consumer warps (tile rows) and points per lane.  FP32
-// state: 16 rows of 64 points (two per lane), twice the warps of an 8 x 128
-// tile for the same shared memory; FP64: 8 rows of 64 points.
-constexpr int kAdjRowsF32 = 16, kAdjVIF32 = 2, kAdjRowsF64 = 8;
+// state: 15 rows of 64 points (two per lane), so that with the producer the
+// CTA has 16 warps, four per SM sub-partition, and each thread may hold 128
+// registers of the sub-partition's 16 K (a 17th warp would put five warps on
+// one sub-partition and cap every thread at 96).  FP64: 8 rows of 64 points.
+constexpr int kAdjRowsF32 = 15, kAdjVIF32 = 2, kAdjRowsF64 = 8;
 
 // Output planes per item: 32, fewer while the grid has too few items to give
 // every SM two.
