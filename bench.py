@@ -56,6 +56,7 @@ WORKLOADS = {
     "large-f64": dict(I=513, J=513, K=1025, sweeps=100, prec="f64"),
     "medium": dict(I=257, J=257, K=513, sweeps=100, prec="f32"),
     "batch": dict(n_grids=512, sweeps=100, prec="f32"),
+    "tuners": dict(n_grids=512, sweeps=100, prec="f32"),
     "adjoint": dict(I=513, J=513, K=1025, sweeps=100, taped=20, C=5, prec="f32"),
     "adjoint-medium": dict(I=257, J=257, K=513, sweeps=40, taped=20, C=5, prec="f32"),
 }
@@ -424,6 +425,50 @@ def bench_batch(args, stream, sweeps=100, steps=3, autotune=True, loops=True, tu
     return out
 
 
+def bench_tuners(stream, sweeps=100):
+    """Launch-plan searches on the 512-grid batch, each from scratch: the
+    default plan, coordinate descent (1 and 2 passes) and the paper's GA
+    (M = T = 10, two seeds).  Reports each plan's rate, plans measured and the
+    search time."""
+    import torch
+
+    import jacobi_inputs as ji
+    from paper_2002_12115_gb300 import JacobiBatch
+    from paper_2002_12115_gb300 import autotune as at
+    dims = ji.batch_dims(512)
+    npts = sum((I - 2) * (J - 2) * (K - 2) for I, J, K in dims)
+    b = JacobiBatch(dims, "f32", 0.8, stream)
+    for g, (I, J, K) in enumerate(dims):
+        b.upload_tensors(g, ji.himeno_fields_torch(I, J, K, seed=42 + g))
+    count = {"n": 0}
+    set_plan = b.set_plan
+
+    def counted(*a, **k):
+        count["n"] += 1
+        return set_plan(*a, **k)
+    b.set_plan = counted
+
+    def rate():
+        b.sweep(sweeps, residuals=False)
+        return npts * sweeps / at.time_call(lambda: b.sweep(sweeps, residuals=False), 3, stream) / 1e9
+
+    set_plan(0, None, None)
+    out = {"default": {"value": rate(), "plans_measured": 0}}
+    runs = (("cd_1pass", lambda: at.tune_batch(b, n_sweeps=10, reps=2, passes=1, cache_path=None)),
+            ("cd_2pass", lambda: at.tune_batch(b, n_sweeps=10, reps=2, passes=2, cache_path=None)),
+            ("ga_seed0", lambda: at.ga_tune_batch(b, M=10, T=10, n_sweeps=10, reps=2, seed=0)),
+            ("ga_seed1", lambda: at.ga_tune_batch(b, M=10, T=10, n_sweeps=10, reps=2, seed=1)))
+    for name, search in runs:
+        count["n"] = 0
+        t0 = time.perf_counter()
+        plan = search()
+        out[name] = {"value": rate(), "plans_measured": count["n"], "search_s": time.perf_counter() - t0,
+                     "plan": {k: plan[k] for k in ("warps", "tile_i", "kdepth")}}
+    b.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def bench_adjoint(args, w, stream, steps=3):
     """n sweeps, then the reverse pass (checkpoint every C) over the last
     `taped` of them, for L = 1/2 |p_T - target|^2."""
@@ -504,6 +549,14 @@ def run_native(args, w, wname):
                                   "frac": r["gbs"] / peak, "peak_kind": peak_kind, "traffic": None,
                                   "kernel": "k_sweep (batched)"},
                      "batch": r, "gpu_launches": args.steps})
+    if wname == "tuners":
+        r = bench_tuners(stream, sweeps=w["sweeps"])
+        return emit({"metric": METRIC + " (512-grid batch under each launch-plan search)",
+                     "value": max(v["value"] for v in r.values()), "unit": UNIT, "n_gpus": world,
+                     "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                     "config": {"workload": "512 grids, dims drawn from {17,33,49,65,97,129}, f32, 100 sweeps; "
+                                            "plans searched from scratch"},
+                     "searches": r})
     if wname.startswith("adjoint"):
         r = bench_adjoint(args, w, stream, steps=args.steps)
         ms = max_over_ranks(r["ms_per_pass"], args.dist)

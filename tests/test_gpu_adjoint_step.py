@@ -82,6 +82,9 @@ CASES = [
     ("f32", (4, 4, 4), 1), ("f32", (33, 33, 65), 0), ("f32", (129, 17, 23), 0), ("f32", (130, 9, 11), 4),
     ("f32", (200, 19, 37), 7), ("f32", (257, 10, 6), 1),
     ("bf16", (129, 17, 23), 0), ("bf16", (257, 9, 12), 5), ("bf16", (50, 30, 20), 3),
+    # FP32 tiles are 64 points x 15 rows: I - 1 a multiple of 64 (the face column is a
+    # tile's extra column) and J one row past a multiple of 15 (a one-row last tile)
+    ("f32", (65, 16, 9), 0), ("f32", (129, 31, 8), 2), ("bf16", (193, 46, 6), 0),
 ]
 
 
