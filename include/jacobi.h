@@ -116,8 +116,10 @@ typedef struct jac_grid {
  * two in [16, 128] (FP64: [16, 64]); W must be 4 or 8, or 16 with BF16
  * coefficients and tile_i >= 32.  Zero fields pick defaults: W = 8 (16 for
  * BF16 on grids a 128-wide tile covers fully), the tile width with the best
- * lane use, and the kdepth that minimises (work-item rounds per CTA) x
- * (kdepth + 3).  Unsupported shapes: JAC_EINVAL at launch. */
+ * lane use, and a kdepth by precision: FP32/BF16 take the smallest depth
+ * (at most 256) at which every work item of a sweep fits one round of CTAs,
+ * else 8; FP64 minimises (work-item rounds per CTA) x (kdepth + 3).
+ * Unsupported shapes: JAC_EINVAL at launch. */
 typedef struct jac_plan {
     int tile_j;   /* rows per work item */
     int kdepth;   /* k-planes per work item, >= 1 */

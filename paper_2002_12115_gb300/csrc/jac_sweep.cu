@@ -216,15 +216,31 @@ int best_tile_i(int I, int J, jac_prec prec, int tj)
     return best;
 }
 
-// k-planes per work item when the plan leaves it open.  A CTA walks its
-// items one after another, so a sweep takes about rounds x (kdepth + h)
-// plane-times, rounds = ceil(items / CTAs), where h = 3 stands for the two
-// extra state planes of an item and the refill of its rings.  Deep items cut
-// that overhead; shallow ones balance the CTAs.  The smallest such cost wins
-// (ties: the deeper item).
-int default_kdepth(long cols, int nk, int ctas)
+// k-planes per work item when the plan leaves it open, by what bounds the
+// sweep (both rules measured on GB300 over 129x129x257 .. 513x513x1025):
+//  * FP32 and BF16 coefficients (memory-bound).  If every item of a sweep
+//    fits in one round of CTAs at a depth of at most 256 planes, the smallest
+//    such depth: each CTA does one item per sweep, so none waits at the
+//    sweep's grid barrier for another's extra item and no ring refills
+//    mid-sweep.  Otherwise shallow items of 8 planes: consecutive items are
+//    row-adjacent tiles of one thin slab of the grid, so the CTAs at work at
+//    any moment read neighbouring rows and share halo planes in L2.
+//  * FP64 (bound by the FP64 pipe).  A sweep takes about rounds x (kdepth +
+//    h) plane-times, rounds = ceil(items / CTAs), h = 3 for an item's two
+//    extra state planes and its ring refill, during which the FP64 pipe
+//    idles; the smallest such cost wins (ties: the deeper item).
+int default_kdepth(long cols, int nk, int ctas, jac_prec prec)
 {
     if (nk <= 1) return 1;
+    if (prec != JAC_F64) {
+        constexpr int kOneRoundMax = 256, kShallow = 8;
+        if (cols <= ctas) {
+            const long kblocks = ctas / cols;   // k-blocks that one round holds
+            const long kd = std::max<long>(2, (nk + kblocks - 1) / kblocks);
+            if (kd <= kOneRoundMax) return (int)std::min<long>(kd, nk);
+        }
+        return std::min(nk, kShallow);
+    }
     const long h = 3;
     int best = 2;
     long best_cost = -1;
@@ -265,7 +281,7 @@ jac_plan resolve_plan(const jac_grid *g, const jac_plan *plan)
     if (p.kdepth == 0) {
         const int ti = std::max(p.tile_i, 1), rows = std::max(p.tile_j, 1);
         const long cols = (long)((g->I - 2) / ti + 1) * ((g->J - 2 + rows - 1) / rows);
-        p.kdepth = default_kdepth(cols, g->K - 2, num_sms());
+        p.kdepth = default_kdepth(cols, g->K - 2, num_sms(), g->prec);
     }
     return p;
 }

@@ -6,8 +6,9 @@ accumulation (+=) on top of nonzero starting values.
 
 Shapes cover one and several tiles in i, j and k, ragged last tiles, the
 face column I-1 falling just past the last tile (I-1 a multiple of the tile
-width: 64 points for FP64, 128 for FP32 storage), work items of one to a few
-output planes (both edge planes in every item), and the smallest grids."""
+width, 64 points), a last row of tiles one row tall (FP32 tiles are 15 rows,
+FP64 tiles 8), work items of one to a few output planes (both edge planes in
+every item), and the smallest grids."""
 import numpy as np
 import pytest
 
