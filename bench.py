@@ -55,6 +55,7 @@ WORKLOADS = {
     "large-bf16": dict(I=513, J=513, K=1025, sweeps=100, prec="bf16"),
     "large-f64": dict(I=513, J=513, K=1025, sweeps=100, prec="f64"),
     "medium": dict(I=257, J=257, K=513, sweeps=100, prec="f32"),
+    "medium-bf16": dict(I=257, J=257, K=513, sweeps=100, prec="bf16"),
     "batch": dict(n_grids=512, sweeps=100, prec="f32"),
     "tuners": dict(n_grids=512, sweeps=100, prec="f32"),
     "adjoint": dict(I=513, J=513, K=1025, sweeps=100, taped=20, C=5, prec="f32"),
@@ -375,8 +376,14 @@ def bench_variant(w, prec, dev, stream, sweeps):
         ms = a.elapsed_time(b)
     gbs = BYTES_PER_POINT[prec] * n_interior(w) / (ms / sweeps * 1e-3) / 1e9
     gpts = n_interior(w) * sweeps / (ms * 1e-3) / 1e9
+    roofline = variant_roofline(prec, gpts)
+    per_sweep = profiled_traffic(f"{w['I']}x{w['J']}x{w['K']} {prec}")
+    if per_sweep:
+        dram = per_sweep / (ms / sweeps * 1e-3) / 1e9
+        roofline.update({"traffic_per_sweep": per_sweep, "dram_achieved": dram,
+                         "dram_frac": dram / measured_peak()[0]})
     return {"value": gpts, "unit": UNIT, "ms_per_sweep": ms / sweeps,
-            "gbs": gbs, "grid": [w["I"], w["J"], w["K"]], "prec": prec, "roofline": variant_roofline(prec, gpts)}
+            "gbs": gbs, "grid": [w["I"], w["J"], w["K"]], "prec": prec, "roofline": roofline}
 
 
 def bench_batch(args, stream, sweeps=100, steps=3, autotune=True, loops=True, tuner="cd"):
