@@ -320,10 +320,15 @@ def bench_single(args, w, stream):
 
 
 def bench_e2e(args, w, jac, stream):
-    """The same step through the C ABI from pinned host FP64 buffers."""
+    """The same step through the C ABI from pinned host FP64 buffers: every
+    step copies its thirteen inputs in, sweeps, reads the residual and copies
+    the state out, all inside the timed region.  Two contexts on two streams
+    take the steps in turn, so one step's host-to-device copies run on the
+    copy engine while the previous step's sweeps run on the SMs."""
     import torch
 
     import jacobi_inputs as ji
+    from paper_2002_12115_gb300 import Jacobi
     I, J, K, n = w["I"], w["J"], w["K"], w["sweeps"]
     fields = ji.himeno_fields(I, J, K)
     host = {}
@@ -331,23 +336,33 @@ def bench_e2e(args, w, jac, stream):
         t = torch.empty(v.shape, dtype=torch.float64, pin_memory=True)
         t.numpy()[...] = v
         host[k] = t.numpy()
-    p_host = torch.empty((K, J, I), dtype=torch.float64, pin_memory=True).numpy()
-    for _ in range(max(1, args.warmup // 2)):
-        jac.upload(host); jac.sweep(n); jac.residual(); jac.download(p_host)
+    p_host = [torch.empty((K, J, I), dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
+    stream2 = torch.cuda.Stream()
+    jac2 = Jacobi(I, J, K, w["prec"], 0.8, stream2)
+    if args.tile_j or args.kdepth or args.tile_i:
+        jac2.set_plan(args.tile_j, args.kdepth, args.tile_i)
+    ctxs = (jac, jac2)
+
+    def run(steps):
+        for k in range(steps):
+            ctxs[k % 2].upload(host)
+            ctxs[k % 2].sweep(n)
+            if k >= 1:                       # finish the previous step meanwhile
+                ctxs[(k - 1) % 2].residual()
+                ctxs[(k - 1) % 2].download(p_host[(k - 1) % 2])
+        ctxs[(steps - 1) % 2].residual()
+        ctxs[(steps - 1) % 2].download(p_host[(steps - 1) % 2])
+
+    run(max(2, args.warmup // 2))
     torch.cuda.synchronize()
     if args.dist is not None:
         args.dist.barrier()
-    c0, c1 = events()
     t0 = time.perf_counter()
-    c0.record(stream)
-    for _ in range(args.steps):
-        jac.upload(host)
-        jac.sweep(n)
-        jac.residual()
-        jac.download(p_host)
-    c1.record(stream)
+    run(args.steps)
     torch.cuda.synchronize()
-    return max(c0.elapsed_time(c1), (time.perf_counter() - t0) * 1e3), host
+    ms = (time.perf_counter() - t0) * 1e3
+    jac2.close()
+    return ms, host
 
 
 def bench_unhoisted(w, jac, host, sweeps=20):
