@@ -277,7 +277,7 @@ jac_status jac_adjoint_step_dev(const jac_grid *g, const void *p_t, const void *
 
 /* Start a checkpoint tape: the next sweeps (at most max_sweeps, across any
  * number of jac_sweep calls) are recorded by saving the state at the start
- * of every C-sweep segment.  Allocates ceil(max_sweeps/C) + C + 2 state
+ * of every C-sweep segment.  Allocates ceil(max_sweeps/C) + C + 1 state
  * arrays.  A new upload or jac_tape_end discards the tape. */
 jac_status jac_tape_begin(jac_ctx *ctx, int C, int max_sweeps);
 jac_status jac_tape_end(jac_ctx *ctx);

@@ -35,11 +35,12 @@ struct jac_ctx {
     // checkpoint tape of the sweeps since jac_tape_begin
     struct Tape {
         int C = 0, max_sweeps = 0, taped = 0;
-        void *mem = nullptr;      // checkpoints, segment states, two lambda buffers, one double
+        void *mem = nullptr;      // checkpoints, segment states 1..C-1, two lambda buffers, one double
         size_t state_bytes = 0;
         int n_ckpt = 0;
         char *ckpt(int s) const { return static_cast<char *>(mem) + (size_t)s * state_bytes; }
-        char *seg(int m) const { return ckpt(n_ckpt) + (size_t)m * state_bytes; }
+        // state m (1 <= m < C) of a segment; state 0 is the segment's checkpoint
+        char *seg(int m) const { return ckpt(n_ckpt) + (size_t)(m - 1) * state_bytes; }
         char *lam(int b) const { return seg(C) + (size_t)b * state_bytes; }
         double *scratch() const { return reinterpret_cast<double *>(lam(2)); }
     } tape;
@@ -334,7 +335,7 @@ jac_status jac_tape_begin(jac_ctx *c, int C, int max_sweeps)
     tp.max_sweeps = max_sweeps;
     tp.state_bytes = array_bytes(c, JAC_P);
     tp.n_ckpt = (max_sweeps + tp.C - 1) / tp.C;
-    const size_t bytes = (size_t)(tp.n_ckpt + tp.C + 2) * tp.state_bytes + 256;
+    const size_t bytes = (size_t)(tp.n_ckpt + tp.C + 1) * tp.state_bytes + 256;
     cudaError_t e = cudaMalloc(&tp.mem, bytes);
     if (e != cudaSuccess) return ctx_fail(c, JAC_ENOMEM, "tape allocation failed (" + std::to_string(bytes) + " bytes)");
     c->tape = tp;
@@ -369,7 +370,7 @@ jac_status jac_sweep_adjoint(jac_ctx *c, const double *lam_T, double *g_wrk1, do
     s = jac::pack_dev(c->I, c->J, c->K, c->prec, JAC_P, lam_T, tp.lam(0), c->stream);
     if (s != JAC_OK) return ctx_from_thread(c, s);
     // faces never change: give every segment slot the faces of the first checkpoint
-    for (int m = 0; m < tp.C; ++m) {
+    for (int m = 1; m < tp.C; ++m) {
         e = cudaMemcpyAsync(tp.seg(m), tp.ckpt(0), tp.state_bytes, cudaMemcpyDeviceToDevice, c->stream);
         if (e != cudaSuccess) return ctx_cuda(c, e, "segment init");
     }
@@ -379,16 +380,16 @@ jac_status jac_sweep_adjoint(jac_ctx *c, const double *lam_T, double *g_wrk1, do
     for (int sgi = nseg - 1; sgi >= 0; --sgi) {
         const int t0 = sgi * tp.C;
         const int len = std::min(tp.C, tp.taped - t0);
-        e = cudaMemcpyAsync(tp.seg(0), tp.ckpt(sgi), tp.state_bytes, cudaMemcpyDeviceToDevice, c->stream);
-        if (e != cudaSuccess) return ctx_cuda(c, e, "checkpoint restore");
+        // state m of this segment: the checkpoint itself for m = 0
+        auto state = [&](int m) -> void * { return m == 0 ? tp.ckpt(sgi) : tp.seg(m); };
         for (int m = 1; m < len; ++m) {          // recompute the segment's states
-            g.p[0] = tp.seg(m - 1);
+            g.p[0] = state(m - 1);
             g.p[1] = tp.seg(m);
             s = jac::sweep_dev(&g, &c->plan, 1, tp.scratch(), c->ws, c->ws_bytes, c->stream);
             if (s != JAC_OK) return ctx_from_thread(c, s);
         }
         for (int m = len - 1; m >= 0; --m) {     // reverse sweeps of the segment
-            s = jac::adjoint_step_dev(&g, tp.seg(m), tp.lam(lc), tp.lam(lc ^ 1), g_wrk1, g_a3, g_coef, 0, c->ws,
+            s = jac::adjoint_step_dev(&g, state(m), tp.lam(lc), tp.lam(lc ^ 1), g_wrk1, g_a3, g_coef, 0, c->ws,
                                       c->ws_bytes, c->stream);
             if (s != JAC_OK) return ctx_from_thread(c, s);
             lc ^= 1;
