@@ -314,6 +314,10 @@ k_adjoint(const __grid_constant__ AdjDesc d)
         for (int e = 0; e < VI; ++e) inI[e] = (ib + e >= 1) && (ib + e <= I - 2);
         const bool inI_l = (it.i0 - 1 >= 1) && (it.i0 - 1 <= I - 2);
         const bool inI_r = (it.i0 + TI >= 1) && (it.i0 + TI <= I - 2);
+        // the tile halo column on this lane's side: lane 0 the left one, the
+        // others the right one (only lane 31 uses it)
+        const int hcol = (lane == 0) ? -1 : TI;
+        const bool hin = (lane == 0) ? inI_l : inI_r;
         bool inJ[3];
 #pragma unroll
         for (int s = 0; s < 3; ++s) inJ[s] = (j - 1 + s >= 1) && (j - 1 + s <= J - 2);
@@ -377,18 +381,16 @@ k_adjoint(const __grid_constant__ AdjDesc d)
                 }
                 T wl = __shfl_up_sync(0xffffffffu, w[s][VI], 1);
                 T wr = __shfl_down_sync(0xffffffffu, w[s][1], 1);
-                if (lane == 0) {
-                    const T mu = (rin && inI_l) ? omega * st_one<G, G::BND, T>(st, row, -1) *
-                                                          st_one<G, G::LAM, T>(st, row, -1)
-                                                : T(0);
-                    wl = st_one<G, G::A3, T>(st, row, -1) * mu;
-                }
-                if (lane == 31) {
-                    const T mu = (rin && inI_r) ? omega * st_one<G, G::BND, T>(st, row, TI) *
-                                                          st_one<G, G::LAM, T>(st, row, TI)
-                                                : T(0);
-                    wr = st_one<G, G::A3, T>(st, row, TI) * mu;
-                    if (s == 1) lam_x = st_one<G, G::LAM, T>(st, row, TI);
+                {
+                    // w at the tile's halo column on this lane's side (lane 0: left,
+                    // the others: right), without a divergent branch; lanes 1..30
+                    // discard it
+                    const T lam_h = st_one<G, G::LAM, T>(st, row, hcol);
+                    const T mu = (rin && hin) ? omega * st_one<G, G::BND, T>(st, row, hcol) * lam_h : T(0);
+                    const T wh = st_one<G, G::A3, T>(st, row, hcol) * mu;
+                    wl = (lane == 0) ? wh : wl;
+                    wr = (lane == 31) ? wh : wr;
+                    if (s == 1) lam_x = lam_h;        // used by lane 31 only
                 }
                 w[s][0] = wl;
                 w[s][VI + 1] = wr;
@@ -405,8 +407,11 @@ k_adjoint(const __grid_constant__ AdjDesc d)
                 for (int e = 0; e < VI; ++e) P2[e] = b2[e] * w[1][e + 1];
                 T l2 = __shfl_up_sync(0xffffffffu, P2[VI - 1], 1);
                 T r2 = __shfl_down_sync(0xffffffffu, P2[0], 1);
-                if (lane == 0) l2 = st_one<G, G::B2, T>(st, r, -1) * w[1][0];
-                if (lane == 31) r2 = st_one<G, G::B2, T>(st, r, TI) * w[1][VI + 1];
+                {
+                    const T p2h = st_one<G, G::B2, T>(st, r, hcol) * (lane == 0 ? w[1][0] : w[1][VI + 1]);
+                    l2 = (lane == 0) ? p2h : l2;
+                    r2 = (lane == 31) ? p2h : r2;
+                }
 #pragma unroll
                 for (int e = 0; e < VI; ++e) {
                     const T lft = (e == 0) ? l2 : P2[e - 1];
@@ -463,16 +468,16 @@ k_adjoint(const __grid_constant__ AdjDesc d)
                 T rbm = __shfl_down_sync(0xffffffffu, Pbm[0], 1);
                 T lbp = __shfl_up_sync(0xffffffffu, Pbp[VI - 1], 1);
                 T rbp = __shfl_down_sync(0xffffffffu, Pbp[0], 1);
-                if (lane == 0) {
-                    la0 = st_one<G, G::A0, T>(st, r, -1) * w[1][0];
-                    lbm = st_one<G, G::B0, T>(st, r - 1, -1) * w[0][0];
-                    lbp = st_one<G, G::B0, T>(st, r + 1, -1) * w[2][0];
+                {
+                    const T bmh = st_one<G, G::B0, T>(st, r - 1, hcol) * (lane == 0 ? w[0][0] : w[0][VI + 1]);
+                    const T bph = st_one<G, G::B0, T>(st, r + 1, hcol) * (lane == 0 ? w[2][0] : w[2][VI + 1]);
+                    lbm = (lane == 0) ? bmh : lbm;
+                    rbm = (lane == 31) ? bmh : rbm;
+                    lbp = (lane == 0) ? bph : lbp;
+                    rbp = (lane == 31) ? bph : rbp;
                 }
-                if (lane == 31) {
-                    rc0 = st_one<G, G::C0, T>(st, r, TI) * w[1][VI + 1];
-                    rbm = st_one<G, G::B0, T>(st, r - 1, TI) * w[0][VI + 1];
-                    rbp = st_one<G, G::B0, T>(st, r + 1, TI) * w[2][VI + 1];
-                }
+                if (lane == 0) la0 = st_one<G, G::A0, T>(st, r, -1) * w[1][0];
+                if (lane == 31) rc0 = st_one<G, G::C0, T>(st, r, TI) * w[1][VI + 1];
 #pragma unroll
                 for (int e = 0; e < VI; ++e) {
                     const T a0w = (e == 0) ? la0 : Pa0[e - 1];
