@@ -287,8 +287,8 @@ def bench_single(args, w, stream):
     dev = device_fields(I, J, K)
     p_dev = torch.empty((K, J, I), dtype=torch.float64, device="cuda")
     jac = Jacobi(I, J, K, prec, 0.8, stream)
-    if args.tile_j or args.kdepth or args.tile_i:
-        jac.set_plan(args.tile_j, args.kdepth, args.tile_i)
+    if args.tile_j or args.kdepth or args.tile_i or args.fuse:
+        jac.set_plan(args.tile_j, args.kdepth, args.tile_i, args.fuse)
     sweep_ev = []
 
     def step(record):
@@ -339,8 +339,8 @@ def bench_e2e(args, w, jac, stream):
     p_host = [torch.empty((K, J, I), dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
     stream2 = torch.cuda.Stream()
     jac2 = Jacobi(I, J, K, w["prec"], 0.8, stream2)
-    if args.tile_j or args.kdepth or args.tile_i:
-        jac2.set_plan(args.tile_j, args.kdepth, args.tile_i)
+    if args.tile_j or args.kdepth or args.tile_i or args.fuse:
+        jac2.set_plan(args.tile_j, args.kdepth, args.tile_i, args.fuse)
     ctxs = (jac, jac2)
 
     def run(steps):
@@ -670,6 +670,8 @@ def main():
     ap.add_argument("--tile-j", type=int, default=0)
     ap.add_argument("--kdepth", type=int, default=0)
     ap.add_argument("--tile-i", type=int, default=0)
+    ap.add_argument("--fuse", type=int, default=0, choices=(0, 1, 2),
+                    help="two-sweep passes for FP32: 0 library's choice, 1 never, 2 always")
     ap.add_argument("--sweeps", type=int, default=0, help="override the workload's sweep count (profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

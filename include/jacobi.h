@@ -124,6 +124,15 @@ typedef struct jac_plan {
     int tile_j;   /* rows per work item */
     int kdepth;   /* k-planes per work item, >= 1 */
     int tile_i;   /* points per row */
+    int fuse;     /* two sweeps per pass (FP32 storage only): 0 the library's
+                     choice, which is single sweeps (on GB300 the two-sweep
+                     pass measured up to 26% slower: it halves the DRAM
+                     traffic but is bound by latency), 1 never, 2 whenever
+                     n_iter >= 4.  A pass reads the state once and writes it
+                     two sweeps later; the state is bitwise that of single
+                     sweeps.  Its tile shape is fixed; tile_i, tile_j and
+                     kdepth then apply to the 0..3 single sweeps that follow
+                     an even number of passes. */
 } jac_plan;
 
 /* Bytes of device workspace jac_sweep_dev needs for this grid and plan. */

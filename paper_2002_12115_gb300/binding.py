@@ -43,7 +43,8 @@ class jac_grid(ctypes.Structure):
 
 
 class jac_plan(ctypes.Structure):
-    _fields_ = [("tile_j", ctypes.c_int), ("kdepth", ctypes.c_int), ("tile_i", ctypes.c_int)]
+    _fields_ = [("tile_j", ctypes.c_int), ("kdepth", ctypes.c_int), ("tile_i", ctypes.c_int),
+                ("fuse", ctypes.c_int)]
 
 
 _VP = ctypes.c_void_p
@@ -196,8 +197,11 @@ class Jacobi:
         return f
 
     # -- the hoisted path
-    def set_plan(self, tile_j: int = 0, kdepth: int = 0, tile_i: int = 0) -> None:
-        self._check(lib().jac_set_plan(self._h, ctypes.byref(jac_plan(int(tile_j), int(kdepth), int(tile_i)))))
+    def set_plan(self, tile_j: int = 0, kdepth: int = 0, tile_i: int = 0, fuse: int = 0) -> None:
+        """Launch plan (0 = default); fuse: 0 library's choice, 1 single sweeps only,
+        2 two-sweep passes (FP32 storage)."""
+        self._check(lib().jac_set_plan(self._h, ctypes.byref(jac_plan(int(tile_j), int(kdepth), int(tile_i),
+                                                                       int(fuse)))))
 
     def upload(self, fields: dict) -> None:
         """Copy in all thirteen host arrays (float64, shape (K, J, I))."""
@@ -281,17 +285,17 @@ class Jacobi:
         self._check(lib().jac_sweep_unhoisted(self._h, int(n), ctypes.byref(f), _VP(_host_ptr(p_host))))
 
 
-def workspace_size(grid: jac_grid, tile_j: int = 0, kdepth: int = 0, tile_i: int = 0) -> int:
+def workspace_size(grid: jac_grid, tile_j: int = 0, kdepth: int = 0, tile_i: int = 0, fuse: int = 0) -> int:
     n = ctypes.c_size_t()
-    check(lib().jac_sweep_workspace_size(ctypes.byref(grid), ctypes.byref(jac_plan(tile_j, kdepth, tile_i)),
+    check(lib().jac_sweep_workspace_size(ctypes.byref(grid), ctypes.byref(jac_plan(tile_j, kdepth, tile_i, fuse)),
                                          ctypes.byref(n)))
     return n.value
 
 
 def sweep_dev(grid: jac_grid, n: int, d_residual: int | None, workspace: int, ws_bytes: int,
-              stream: int, tile_j: int = 0, kdepth: int = 0, tile_i: int = 0) -> None:
+              stream: int, tile_j: int = 0, kdepth: int = 0, tile_i: int = 0, fuse: int = 0) -> None:
     """The stateless entry point jac_sweep_dev on caller-owned device buffers."""
-    check(lib().jac_sweep_dev(ctypes.byref(grid), ctypes.byref(jac_plan(tile_j, kdepth, tile_i)), int(n),
+    check(lib().jac_sweep_dev(ctypes.byref(grid), ctypes.byref(jac_plan(tile_j, kdepth, tile_i, fuse)), int(n),
                               _VP(d_residual) if d_residual else None, _VP(workspace), ctypes.c_size_t(ws_bytes),
                               _VP(stream)))
 

@@ -97,6 +97,7 @@ jac_plan grid_plan(const jac_batch *b, int g)
 {
     const int full = 32 * jac::vector_points(b->prec);
     jac_plan p;
+    p.fuse = 1;   // batched grids sweep one sweep per pass
     p.tile_i = b->tile_i[g] > 0 ? b->tile_i[g] : jac::best_tile_i(b->I[g], b->J[g], b->prec, b->warps);
     p.tile_j = b->warps * (full / p.tile_i);
     p.kdepth = b->kdepth[g];

@@ -27,7 +27,7 @@ struct jac_ctx {
     double *staging = nullptr;        // I*J*K doubles
     void *ws = nullptr;               // sweep workspace
     size_t ws_bytes = 0;
-    jac_plan plan{0, 0, 0};
+    jac_plan plan{0, 0, 0, 0};
     long long count = 0;
     bool uploaded = false;
     bool has_res = false;
@@ -252,9 +252,10 @@ const char *jac_last_error(const jac_ctx *c) { return c ? c->err.c_str() : jac::
 jac_status jac_set_plan(jac_ctx *c, const jac_plan *plan)
 {
     if (!c) return ctx_fail(c, JAC_EINVAL, "ctx is NULL");
-    jac_plan p{0, 0, 0};
+    jac_plan p{0, 0, 0, 0};
     if (plan) p = *plan;
     if (p.tile_j < 0 || p.tile_i < 0 || p.kdepth < 0) return ctx_fail(c, JAC_EINVAL, "negative plan entry");
+    if (p.fuse < 0 || p.fuse > 2) return ctx_fail(c, JAC_EINVAL, "fuse must be 0, 1 or 2");
     if (p.tile_i || p.tile_j) {
         jac_grid g = make_grid(c);
         int rw = 0, tj = 0;

@@ -37,6 +37,12 @@ jac_status build_desc(GridDesc *d, const jac_grid *g, const jac_plan &p, int ite
 template <bool BATCH>
 jac_status launch_sweep(jac_prec prec, int tj, const GridDesc &d0, const SweepArgs &a, unsigned nblocks,
                         cudaStream_t st);
+// Two-sweep passes (FP32 storage): n_pass passes of two sweeps each, in one
+// cooperative launch; the residual of the last sweep to d_residual (NULL:
+// none).  kdepth 0: the default depth.
+jac_status sweep2_run(const jac_grid *g, int kdepth, int n_pass, double *d_residual, void *workspace,
+                      size_t ws_bytes, cudaStream_t st);
+size_t sweep2_workspace_bytes(const jac_grid *g);
 jac_status adjoint_step_dev(const jac_grid *g, const void *p_t, const void *lam_in, void *lam_out, double *g_wrk1,
                             double *g_a3, double *const *g_coef, int kdepth, void *workspace, size_t ws_bytes,
                             cudaStream_t st);

@@ -260,6 +260,7 @@ jac_plan resolve_plan(const jac_grid *g, const jac_plan *plan)
     const int vi = vector_points(g->prec), full = 32 * vi;
     int tj = 8;
     jac_plan p;
+    p.fuse = plan ? plan->fuse : 0;
     p.tile_i = (plan && plan->tile_i > 0) ? plan->tile_i : 0;
     p.tile_j = (plan && plan->tile_j > 0) ? plan->tile_j : 0;
     p.kdepth = (plan && plan->kdepth > 0) ? plan->kdepth : 0;
@@ -419,7 +420,16 @@ size_t sweep_workspace_bytes(const jac_grid *g, const jac_plan &p)
     const long long items = (long long)((g->I - 2) / ti + 1) * ((g->J - 2 + rows - 1) / rows) *
                             ((g->K - 2 + kd - 1) / kd);
     const long long blocks = std::min<long long>(items, num_sms());
-    return kWsHeaderBytes + round_up((size_t)blocks * sizeof(double), 256);
+    const size_t single = kWsHeaderBytes + round_up((size_t)blocks * sizeof(double), 256);
+    if (g->prec != JAC_F32 || p.fuse == 1) return single;
+    return std::max(single, sweep2_workspace_bytes(g));   // two-sweep passes may run
+}
+
+// Whether a call of n_iter sweeps runs as two-sweep passes.
+bool use_two_sweep_passes(const jac_grid *g, const jac_plan &p, int n_iter)
+{
+    if (g->prec != JAC_F32 || p.fuse == 1 || n_iter < 4) return false;
+    return p.fuse == 2;
 }
 
 jac_status sweep_dev(const jac_grid *g, const jac_plan *plan, int n_iter, double *d_residual, void *workspace,
@@ -432,9 +442,22 @@ jac_status sweep_dev(const jac_grid *g, const jac_plan *plan, int n_iter, double
     const jac_plan p = resolve_plan(g, plan);
     int rw = 0, tj = 0;
     if ((s = check_plan(g->prec, p, &rw, &tj)) != JAC_OK) return s;
+    if (p.fuse < 0 || p.fuse > 2) return fail(JAC_EINVAL, "fuse must be 0, 1 or 2");
     if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 15)) return fail(JAC_EINVAL, "bad workspace");
     const size_t need = sweep_workspace_bytes(g, p);
     if (ws_bytes < need) return fail(JAC_EINVAL, "workspace too small: need " + std::to_string(need) + " bytes");
+    if (use_two_sweep_passes(g, p, n_iter)) {
+        // an even number of passes keeps the state of n sweeps in p[n % 2];
+        // the remaining 0..3 sweeps run singly and give the residual if any
+        const int n_pass = (n_iter / 2) & ~1;
+        const int rest = n_iter - 2 * n_pass;
+        double *res2 = nullptr;
+        if (rest == 0) res2 = d_residual ? d_residual : &static_cast<WsHeader *>(workspace)->residual;
+        if ((s = sweep2_run(g, 0, n_pass, res2, workspace, ws_bytes, static_cast<cudaStream_t>(stream))) != JAC_OK)
+            return s;
+        if (rest == 0) return JAC_OK;
+        n_iter = rest;
+    }
     GridDesc d0;
     if ((s = build_desc(&d0, g, p, 0)) != JAC_OK) return s;
     WsHeader *hdr = static_cast<WsHeader *>(workspace);

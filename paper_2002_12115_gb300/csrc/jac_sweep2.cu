@@ -1,0 +1,587 @@
+// Two fused sweeps per pass (temporal blocking by two) for FP32 storage.
+//
+// A pass reads the state p_t and writes p_{t+2}; the intermediate state
+// p_{t+1} of a tile lives only in shared memory.  Every coefficient plane is
+// then read from memory once for two point-updates.  Each update is the
+// same arithmetic as the single-sweep kernel (ss_f32), so a pass gives
+// bitwise the state of two single sweeps.
+//
+// Kernel design (persistent, warp-specialised, one CTA per SM, all passes of
+// a call in one cooperative launch):
+//   * an item is a tile of 128 columns x R2 = 8 rows in (i, j) of output
+//     points over `kdepth` output planes kb .. ke-1.  Sweep 1 runs over the
+//     tile's 128 columns, the R1 = R2 + 2 rows j0-1 .. j0+R2 and the planes
+//     kb-1 .. ke; sweep 2 over the R2 inner rows and planes kb .. ke-1, and
+//     it is valid on columns i0+1 .. i0+126 (its neighbours must lie in
+//     sweep 1's columns), so tiles advance by 124 columns and overlap.  A
+//     tile owns (stores, and counts in the residual) columns i0+1 .. i0+124,
+//     the last tile of a row up to I-2.  When the column past the tile is
+//     the face I-1, its value never changes, and lane 31 keeps it from
+//     sweep 1's state reads, so the last tile reaches column I-2 = i0+127;
+//   * warp 10 (one lane) copies the planes of p_t, with a halo of 4 columns
+//     and 2 rows, into a ring of 4 slots; before pass t >= 1 it waits on the
+//     grid barrier of the pass before;
+//   * warp 11 (one lane) copies the twelve coefficient tiles (128 x R1) of
+//     every sweep-1 plane into a ring of 3 stages.  A stage serves sweep 1
+//     at plane m and, one step later, sweep 2 at plane m, so it is released
+//     only after both;
+//   * consumer warp w (0 .. R1-1) owns row j0-1+w.  At step s (plane
+//     m = kb-1+s) it computes sweep 1 there into a ring of 4 intermediate
+//     planes, and (warps 1 .. R1-2, s >= 2) sweep 2 at plane m-1 from the
+//     intermediate planes m-2 .. m, which every warp has written (an
+//     mbarrier per intermediate plane);
+//   * the residual of the last pass's second sweep is reduced as in the
+//     single-sweep kernel; every wait is bounded.
+//
+// Measured on GB300 against the single-sweep kernel (FP32, Gpoint-updates/s):
+// 129x129x257 126 against 129, 513x513x1025 110 against 114, 257x257x513 88
+// against 119 (three 128-column tiles per 257-point row leave a third of the
+// lanes idle).  On 129x129x257 a pass moves 98 MB per sweep from DRAM against
+// 187 MB, but it executes 17% more instructions (halo rows and planes) and
+// waits at every step for all warps' intermediate rows, so it is bound by
+// latency at 47% issue; the shared memory holds one 61 KB coefficient stage
+// in flight.  An L2 prefetch of the stages ahead and per-row barriers were
+// both slower.  The library therefore runs single sweeps unless asked.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "jac_internal.h"
+#include "jac_sweep_kernel.cuh"
+
+namespace jac {
+
+struct Sweep2Shape {
+    static constexpr int VI = 4, TI = 128, H = 4;
+    static constexpr int R2 = 8, R1 = R2 + 2;                // output rows, sweep-1 rows (= consumer warps)
+    static constexpr int ADV = TI - 4;                       // tile advance in i
+    static constexpr int PW = TI + 2 * H, PH = R1 + 2;       // state plane box
+    static constexpr int P_BYTES = PW * PH * 4;              // 6528
+    static constexpr int TILE = TI * R1 * 4;                 // one coefficient tile, 5120
+    static constexpr int C_BYTES = 12 * TILE;                // one stage
+    static constexpr int Q_BYTES = TI * R1 * 4;              // one intermediate plane
+    static constexpr int RP = 4, RC = 3, RQ = 4;
+    static constexpr size_t SMEM = (size_t)RP * P_BYTES + (size_t)RQ * Q_BYTES + (size_t)RC * C_BYTES + 128;
+    static constexpr int THREADS = 32 * (R1 + 2);
+    static_assert(P_BYTES % 128 == 0 && Q_BYTES % 128 == 0 && C_BYTES % 128 == 0, "slot alignment");
+};
+
+struct Sweep2Desc {
+    CUtensorMap p[2];          // state buffers, box (PW, PH, 1)
+    CUtensorMap coef[12];      // JAC_A0 .. JAC_BND (index q-1), box (TI, R1, 1)
+    void *p_buf[2];
+    int I, J, K, pitch;
+    int kdepth, nti, ntj, nkb, nitems;
+};
+
+struct Sweep2Args {
+    int n_pass, par;           // pass t reads p[(t + par) & 1], writes the other
+    double omega;
+    double *partials;          // gridDim.x
+    double *res;               // residual of the last pass's second sweep (NULL: none)
+    WsHeader *hdr;
+    int l2_keep_state;
+    unsigned l2_keep_coef;
+};
+
+struct Item2 {
+    int ti, i0, j0, kb, nout;
+};
+
+__device__ __forceinline__ Item2 decode_item2(const Sweep2Desc &d, int item)
+{
+    using S = Sweep2Shape;
+    Item2 it;
+    const int tj = item % d.ntj;
+    const int r = item / d.ntj;
+    it.ti = r % d.nti;
+    const int kk = r / d.nti;
+    it.i0 = it.ti * S::ADV;
+    it.j0 = 1 + tj * S::R2;
+    it.kb = 1 + kk * d.kdepth;
+    it.nout = min(d.K - 1, it.kb + d.kdepth) - it.kb;
+    return it;
+}
+
+// VI values of an intermediate-plane row (no halo) with the left and right
+// neighbours by lane shuffles; the edge lanes get `left` / `right`.
+__device__ __forceinline__ void q_ext(const float *row, int lane, float left, float right, float (&e)[6])
+{
+    const float4 v = *reinterpret_cast<const float4 *>(row + 4 * lane);
+    e[1] = v.x; e[2] = v.y; e[3] = v.z; e[4] = v.w;
+    const float l = __shfl_up_sync(0xffffffffu, e[4], 1);
+    const float r = __shfl_down_sync(0xffffffffu, e[1], 1);
+    e[0] = (lane == 0) ? left : l;
+    e[5] = (lane == 31) ? right : r;
+}
+
+__global__ void __launch_bounds__(Sweep2Shape::THREADS, 1)
+k_sweep2(const __grid_constant__ Sweep2Desc d, const Sweep2Args a)
+{
+    using S = Sweep2Shape;
+    constexpr int VI = S::VI, TI = S::TI, H = S::H, R1 = S::R1, RP = S::RP, RC = S::RC, RQ = S::RQ;
+    extern __shared__ unsigned char dsm2_raw[];
+    unsigned char *base =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(dsm2_raw) + 127) & ~uintptr_t(127));
+    unsigned char *ring_q = base + (size_t)RP * S::P_BYTES;
+    unsigned char *ring_c = ring_q + (size_t)RQ * S::Q_BYTES;
+    __shared__ __align__(8) uint64_t p_full[RP], p_empty[RP], c_full[RC], c_empty[RC], q_full[RQ], q_empty[RQ],
+        cons_bar;
+    __shared__ volatile int s_abort;
+    __shared__ double s_part[R1];
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int G = gridDim.x;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < RP; ++s) { mbar_init(&p_full[s], 1); mbar_init(&p_empty[s], R1); }
+        for (int s = 0; s < RC; ++s) { mbar_init(&c_full[s], 1); mbar_init(&c_empty[s], R1); }
+        for (int s = 0; s < RQ; ++s) { mbar_init(&q_full[s], R1); mbar_init(&q_empty[s], R1); }
+        mbar_init(&cons_bar, R1);
+        s_abort = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == R1 + 1) {
+        // ------------------------------------------------ coefficient producer
+        if (lane == 0) {
+            const uint64_t pol = l2_policy(a.l2_keep_state ? -1 : 0);
+            const uint64_t pol_keep = l2_policy(1);
+            uint32_t cc = 0;
+            bool ok = true;
+            for (int t = 0; t < a.n_pass && ok; ++t)
+                for (int item = blockIdx.x; item < d.nitems && ok; item += G) {
+                    const Item2 it = decode_item2(d, item);
+                    for (int q = 0; q < it.nout + 2; ++q, ++cc) {
+                        const uint32_t slot = cc % RC, use = cc / RC;
+                        if (use > 0 && !mbar_wait_bounded(&c_empty[slot], (use - 1) & 1)) { ok = false; break; }
+                        if (s_abort) { ok = false; break; }
+                        unsigned char *st = ring_c + (size_t)slot * S::C_BYTES;
+                        mbar_arrive_expect_tx(&c_full[slot], (uint32_t)S::C_BYTES);
+                        for (int k = JAC_A0; k <= JAC_BND; ++k)
+                            tma_load_3d_hint(st + (size_t)(k - 1) * S::TILE, &d.coef[k - 1], &c_full[slot], it.i0,
+                                             it.j0 - 1, it.kb - 1 + q, ((a.l2_keep_coef >> k) & 1u) ? pol_keep : pol);
+                    }
+                }
+            if (!ok) {
+                s_abort = 1;
+                atomicExch(&a.hdr->errword, (int)JAC_ETIMEOUT);
+            }
+            for (uint32_t s = 0; s < (uint32_t)RC && s < cc; ++s) {   // land every issued copy
+                const uint32_t last = cc - 1 - ((cc - 1 - s) % RC);
+                (void)mbar_wait_bounded(&c_full[s], (last / RC) & 1);
+            }
+        }
+    } else if (warp == R1) {
+        // ------------------------------------------------------ state producer
+        if (lane == 0) {
+            const uint64_t pol = l2_policy(a.l2_keep_state ? 1 : 0);
+            uint32_t pc = 0;
+            bool ok = true;
+            for (int t = 0; t < a.n_pass && ok; ++t) {
+                if (t > 0) {
+                    if (!wait_counter_bounded(&a.hdr->gbar, (unsigned)t * G)) { ok = false; break; }
+                    fence_proxy_async_global();
+                }
+                const CUtensorMap *pm = ((t + a.par) & 1) ? &d.p[1] : &d.p[0];
+                for (int item = blockIdx.x; item < d.nitems && ok; item += G) {
+                    const Item2 it = decode_item2(d, item);
+                    for (int q = 0; q < it.nout + 4; ++q, ++pc) {
+                        const uint32_t slot = pc % RP, use = pc / RP;
+                        if (use > 0 && !mbar_wait_bounded(&p_empty[slot], (use - 1) & 1)) { ok = false; break; }
+                        if (s_abort) { ok = false; break; }
+                        mbar_arrive_expect_tx(&p_full[slot], (uint32_t)S::P_BYTES);
+                        tma_load_3d_hint(base + (size_t)slot * S::P_BYTES, pm, &p_full[slot], it.i0 - H, it.j0 - 2,
+                                         it.kb - 2 + q, pol);
+                    }
+                }
+            }
+            if (!ok) {
+                s_abort = 1;
+                atomicExch(&a.hdr->errword, (int)JAC_ETIMEOUT);
+            }
+            for (uint32_t s = 0; s < (uint32_t)RP && s < pc; ++s) {
+                const uint32_t last = pc - 1 - ((pc - 1 - s) % RP);
+                (void)mbar_wait_bounded(&p_full[s], (last / RP) & 1);
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ consumers
+        const int w = warp;                         // row j0-1+w of every item
+        const float omega = (float)a.omega;
+        const uint64_t st_pol = l2_policy(a.l2_keep_state ? 1 : 0);
+        const int I = d.I, J = d.J, K = d.K, pitch = d.pitch;
+        uint32_t pc = 0, cc = 0, qc = 0;
+        bool ok = true;
+        double acc = 0.0;
+        uint32_t sync_phase = 0;
+        auto cons_sync = [&]() -> bool {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&cons_bar);
+            const bool r = mbar_wait_bounded(&cons_bar, sync_phase & 1);
+            ++sync_phase;
+            return __all_sync(0xffffffffu, r);
+        };
+        const bool do2 = (w >= 1) && (w <= R1 - 2);  // this warp's row is an output row too
+
+        for (int t = 0; t < a.n_pass && ok; ++t) {
+            const bool res = (t == a.n_pass - 1) && (a.res != nullptr);
+            float *p_out = static_cast<float *>(((t + 1 + a.par) & 1) ? d.p_buf[1] : d.p_buf[0]);
+            for (int item = blockIdx.x; item < d.nitems && ok; item += G) {
+                const Item2 it = decode_item2(d, item);
+                const int j = it.j0 - 1 + w;
+                const int ib = it.i0 + VI * lane;
+                const bool last_ti = (it.ti == d.nti - 1);
+                const int own_hi = last_ti ? I - 2 : it.i0 + S::ADV;
+                const bool row1_in = (j >= 1) && (j <= J - 2);
+                bool in_i[VI], owned[VI];
+#pragma unroll
+                for (int e = 0; e < VI; ++e) {
+                    in_i[e] = (ib + e >= 1) && (ib + e <= I - 2);
+                    owned[e] = do2 && row1_in && in_i[e] && (ib + e >= it.i0 + 1) && (ib + e <= own_hi);
+                }
+                bool all_owned = true;
+#pragma unroll
+                for (int e = 0; e < VI; ++e) all_owned = all_owned && owned[e];
+                const int r0 = w * S::PW, r1 = (w + 1) * S::PW, r2 = (w + 2) * S::PW;   // rows j-1, j, j+1
+                const int cidx = w * TI + VI * lane;
+                // the face column I-1 just past the tile: its state never
+                // changes; lane 31 keeps it from sweep 1's reads, per plane
+                // (the last three planes) and row (j-1, j, j+1)
+                float fh[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+
+                for (int s = 0; s < it.nout + 2; ++s) {
+                    const int m = it.kb - 1 + s;                 // sweep-1 plane
+                    // ---- sweep 1 at plane m, row j, into intermediate plane s
+                    if (s == 0) {
+                        ok = mbar_wait_bounded(&p_full[pc % RP], (pc / RP) & 1) &&
+                             mbar_wait_bounded(&p_full[(pc + 1) % RP], ((pc + 1) / RP) & 1);
+                    }
+                    const uint32_t q2 = pc + s + 2;
+                    ok = ok && mbar_wait_bounded(&p_full[q2 % RP], (q2 / RP) & 1);
+                    ok = ok && mbar_wait_bounded(&c_full[(cc + s) % RC], ((cc + s) / RC) & 1);
+                    const uint32_t qs = qc + s;
+                    if (qs >= RQ) ok = ok && mbar_wait_bounded(&q_empty[qs % RQ], ((qs / RQ) - 1) & 1);
+                    ok = __all_sync(0xffffffffu, ok && !s_abort);
+                    if (!ok) break;
+                    {
+                        const float *Pm = reinterpret_cast<const float *>(base + (size_t)((pc + s) % RP) * S::P_BYTES);
+                        const float *Pk =
+                            reinterpret_cast<const float *>(base + (size_t)((pc + s + 1) % RP) * S::P_BYTES);
+                        const float *Pp = reinterpret_cast<const float *>(base + (size_t)(q2 % RP) * S::P_BYTES);
+                        const unsigned char *cs = ring_c + (size_t)((cc + s) % RC) * S::C_BYTES;
+                        float ek0[VI + 2], ek1[VI + 2], ek2[VI + 2], em1[VI + 2], ep1[VI + 2];
+                        float vm0[VI], vm2[VI], vp0[VI], vp2[VI];
+                        load_ext<float, VI, H>(Pk + r0, lane, 32, ek0);
+                        load_ext<float, VI, H>(Pk + r1, lane, 32, ek1);
+                        load_ext<float, VI, H>(Pk + r2, lane, 32, ek2);
+                        load_ext<float, VI, H>(Pm + r1, lane, 32, em1);
+                        load_ext<float, VI, H>(Pp + r1, lane, 32, ep1);
+                        lds_vec<float, VI>(Pm + r0 + H + VI * lane, vm0);
+                        lds_vec<float, VI>(Pm + r2 + H + VI * lane, vm2);
+                        lds_vec<float, VI>(Pp + r0 + H + VI * lane, vp0);
+                        lds_vec<float, VI>(Pp + r2 + H + VI * lane, vp2);
+                        float ca0[VI], ca1[VI], ca2[VI], ca3[VI], cb0[VI], cb1[VI], cb2[VI], cc0[VI], cc1[VI],
+                            cc2[VI], cwk[VI], cbn[VI];
+                        lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 0 * S::TILE) + cidx, ca0);
+                        lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 1 * S::TILE) + cidx, ca1);
+                        lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 2 * S::TILE) + cidx, ca2);
+                        lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 3 * S::TILE) + cidx, ca3);
+                        lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 4 * S::TILE) + cidx, cb0);
+                        lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 5 * S::TILE) + cidx, cb1);
+                        lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 6 * S::TILE) + cidx, cb2);
+                        lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 7 * S::TILE) + cidx, cc0);
+                        lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 8 * S::TILE) + cidx, cc1);
+                        lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 9 * S::TILE) + cidx, cc2);
+                        lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 10 * S::TILE) + cidx, cwk);
+                        lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 11 * S::TILE) + cidx, cbn);
+                        const bool in1 = row1_in && (m >= 1) && (m <= K - 2);
+                        float out[VI];
+#pragma unroll
+                        for (int e = 0; e < VI; ++e) {
+                            const float c = ek1[e + 1];
+                            const float bij = ((ek2[e + 2] - ek0[e + 2]) - ek2[e]) + ek0[e];
+                            const float bjk = ((vp2[e] - vm2[e]) - vp0[e]) + vm0[e];
+                            const float bik = ((ep1[e + 2] - em1[e + 2]) - ep1[e]) + em1[e];
+                            const float ss = ss_f32<false>(c, ek1[e + 2], ek1[e], ek2[e + 1], ek0[e + 1], ep1[e + 1],
+                                                           em1[e + 1], bij, bjk, bik, ca0[e], ca1[e], ca2[e], ca3[e],
+                                                           cb0[e], cb1[e], cb2[e], cc0[e], cc1[e], cc2[e], cwk[e],
+                                                           cbn[e]);
+                            out[e] = (in1 && in_i[e]) ? fmaf(omega, ss, c) : c;
+                        }
+                        float *qrow = reinterpret_cast<float *>(ring_q + (size_t)(qs % RQ) * S::Q_BYTES) + w * TI;
+                        *reinterpret_cast<float4 *>(qrow + VI * lane) = make_float4(out[0], out[1], out[2], out[3]);
+                        // face history: planes m-2, m-1, m at column i0+128
+                        fh[0][0] = fh[1][0]; fh[0][1] = fh[1][1]; fh[0][2] = fh[1][2];
+                        fh[1][0] = fh[2][0]; fh[1][1] = fh[2][1]; fh[1][2] = fh[2][2];
+                        fh[2][0] = ek0[VI + 1]; fh[2][1] = ek1[VI + 1]; fh[2][2] = ek2[VI + 1];
+                    }
+                    __syncwarp();
+                    if (lane == 0) {
+                        mbar_arrive(&q_full[qs % RQ]);            // intermediate plane s: this row written
+                        mbar_arrive(&p_empty[(pc + s) % RP]);     // state plane m-1 is done
+                    }
+
+                    // ---- sweep 2 at plane m-1 from intermediate planes s-2 .. s
+                    if (s >= 2) {
+                        for (int qq = 0; qq < 3 && ok; ++qq) {
+                            const uint32_t qw = qc + s - 2 + qq;
+                            ok = mbar_wait_bounded(&q_full[qw % RQ], (qw / RQ) & 1);
+                        }
+                        ok = __all_sync(0xffffffffu, ok && !s_abort);
+                        if (!ok) break;
+                        if (do2) {
+                            const int m2 = m - 1;
+                            const float *Qm =
+                                reinterpret_cast<const float *>(ring_q + (size_t)((qc + s - 2) % RQ) * S::Q_BYTES);
+                            const float *Qk =
+                                reinterpret_cast<const float *>(ring_q + (size_t)((qc + s - 1) % RQ) * S::Q_BYTES);
+                            const float *Qp = reinterpret_cast<const float *>(ring_q + (size_t)(qs % RQ) * S::Q_BYTES);
+                            const unsigned char *cs = ring_c + (size_t)((cc + s - 1) % RC) * S::C_BYTES;
+                            const int q0 = (w - 1) * TI, q1 = w * TI, q2r = (w + 1) * TI;
+                            // column i0-1 is never needed (column i0 is not owned);
+                            // column i0+128 only as the face I-1
+                            float ek0[VI + 2], ek1[VI + 2], ek2[VI + 2], em1[VI + 2], ep1[VI + 2];
+                            float vm0[VI], vm2[VI], vp0[VI], vp2[VI];
+                            q_ext(Qk + q0, lane, 0.f, fh[1][0], ek0);
+                            q_ext(Qk + q1, lane, 0.f, fh[1][1], ek1);
+                            q_ext(Qk + q2r, lane, 0.f, fh[1][2], ek2);
+                            q_ext(Qm + q1, lane, 0.f, fh[0][1], em1);
+                            q_ext(Qp + q1, lane, 0.f, fh[2][1], ep1);
+                            lds_vec<float, VI>(Qm + q0 + VI * lane, vm0);
+                            lds_vec<float, VI>(Qm + q2r + VI * lane, vm2);
+                            lds_vec<float, VI>(Qp + q0 + VI * lane, vp0);
+                            lds_vec<float, VI>(Qp + q2r + VI * lane, vp2);
+                            float ca0[VI], ca1[VI], ca2[VI], ca3[VI], cb0[VI], cb1[VI], cb2[VI], cc0[VI], cc1[VI],
+                                cc2[VI], cwk[VI], cbn[VI];
+                            lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 0 * S::TILE) + cidx, ca0);
+                            lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 1 * S::TILE) + cidx, ca1);
+                            lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 2 * S::TILE) + cidx, ca2);
+                            lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 3 * S::TILE) + cidx, ca3);
+                            lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 4 * S::TILE) + cidx, cb0);
+                            lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 5 * S::TILE) + cidx, cb1);
+                            lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 6 * S::TILE) + cidx, cb2);
+                            lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 7 * S::TILE) + cidx, cc0);
+                            lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 8 * S::TILE) + cidx, cc1);
+                            lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 9 * S::TILE) + cidx, cc2);
+                            lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 10 * S::TILE) + cidx, cwk);
+                            lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 11 * S::TILE) + cidx, cbn);
+                            float out[VI];
+                            float ss2 = 0.0f;
+#pragma unroll
+                            for (int e = 0; e < VI; ++e) {
+                                const float c = ek1[e + 1];
+                                const float bij = ((ek2[e + 2] - ek0[e + 2]) - ek2[e]) + ek0[e];
+                                const float bjk = ((vp2[e] - vm2[e]) - vp0[e]) + vm0[e];
+                                const float bik = ((ep1[e + 2] - em1[e + 2]) - ep1[e]) + em1[e];
+                                const float ss = ss_f32<false>(c, ek1[e + 2], ek1[e], ek2[e + 1], ek0[e + 1],
+                                                               ep1[e + 1], em1[e + 1], bij, bjk, bik, ca0[e], ca1[e],
+                                                               ca2[e], ca3[e], cb0[e], cb1[e], cb2[e], cc0[e], cc1[e],
+                                                               cc2[e], cwk[e], cbn[e]);
+                                out[e] = owned[e] ? fmaf(omega, ss, c) : c;
+                                if (res && owned[e]) ss2 = fmaf(ss, ss, ss2);
+                            }
+                            if (res) acc += (double)ss2;
+                            const size_t off = ((size_t)m2 * J + (size_t)j) * (size_t)pitch + (size_t)ib;
+                            if (all_owned) {
+                                store_vec<float, VI>(p_out + off, out, st_pol);
+                            } else {
+#pragma unroll
+                                for (int e = 0; e < VI; ++e)
+                                    if (owned[e]) p_out[off + e] = out[e];
+                            }
+                        }
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&q_empty[(qc + s - 2) % RQ]);   // intermediate plane s-2 done
+                    }
+                    if (s >= 1) {
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&c_empty[(cc + s - 1) % RC]);  // stage s-1: both sweeps done
+                    }
+                }
+                if (!ok) break;
+                // the item's last state planes, stage and intermediate planes
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&p_empty[(pc + it.nout + 2) % RP]);
+                    mbar_arrive(&p_empty[(pc + it.nout + 3) % RP]);
+                    mbar_arrive(&c_empty[(cc + it.nout + 1) % RC]);
+                    mbar_arrive(&q_empty[(qc + it.nout) % RQ]);
+                    mbar_arrive(&q_empty[(qc + it.nout + 1) % RQ]);
+                }
+                pc += it.nout + 4;
+                cc += it.nout + 2;
+                qc += it.nout + 2;
+            }
+            if (!ok) break;
+            if (res) {
+                double v = acc;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                if (lane == 0) s_part[w] = v;
+                if (!cons_sync()) { ok = false; break; }
+                if (threadIdx.x == 0) {
+                    double sum = 0.0, comp = 0.0;
+                    for (int q = 0; q < R1; ++q) neumaier_add(sum, comp, s_part[q]);
+                    a.partials[blockIdx.x] = sum + comp;
+                }
+                acc = 0.0;
+                if (!cons_sync()) { ok = false; break; }
+            }
+            if (t + 1 < a.n_pass) {
+                // publish this CTA's part of the pass to every CTA's TMA reads
+                fence_proxy_async_global();
+                if (!cons_sync()) { ok = false; break; }
+                if (threadIdx.x == 0) {
+                    __threadfence();
+                    atomicAdd(&a.hdr->gbar, 1u);
+                }
+            }
+        }
+        if (!ok) {
+            s_abort = 1;
+            atomicExch(&a.hdr->errword, (int)JAC_ETIMEOUT);
+        }
+    }
+
+    // CTA epilogue: the last CTA to finish sums the partials in CTA order
+    // and resets the workspace counters for the next launch.
+    __syncthreads();
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&a.hdr->counter, 1u);
+        s_last = (prev == (unsigned)G - 1);
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        if (threadIdx.x == 0) {
+            if (a.res != nullptr && !s_abort) {
+                double sum = 0.0, comp = 0.0;
+                for (int b = 0; b < G; ++b) neumaier_add(sum, comp, __ldcg(&a.partials[b]));
+                *a.res = sum + comp;
+            }
+            a.hdr->gbar = 0u;
+            a.hdr->counter = 0u;
+            __threadfence();
+        }
+    }
+}
+
+// ------------------------------------------------------------ host side
+namespace {
+
+jac_status fail2(jac_status st, const std::string &msg)
+{
+    set_thread_error(msg);
+    return st;
+}
+
+}  // namespace
+
+// Tiles in i: the smallest count whose last tile reaches column I-2, either
+// within sweep 2's valid columns (i0 + 126) or, when the column past the
+// tile is the face I-1, at i0 + 127.
+int sweep2_tiles_i(int I)
+{
+    using S = Sweep2Shape;
+    for (int n = 1;; ++n) {
+        const int i0 = (n - 1) * S::ADV;
+        if (i0 + 126 >= I - 2 || i0 + 128 == I - 1) return n;
+    }
+}
+
+int sweep2_kdepth(long cols, int nk, int ctas)
+{
+    // one round of items when it fits at a depth of at most 256, else 16
+    if (nk <= 1) return 1;
+    if (cols <= ctas) {
+        const long kblocks = ctas / cols;
+        const long kd = std::max<long>(2, (nk + kblocks - 1) / kblocks);
+        if (kd <= 256) return (int)std::min<long>(kd, nk);
+    }
+    return std::min(nk, 16);
+}
+
+size_t sweep2_workspace_bytes(const jac_grid *g)
+{
+    using S = Sweep2Shape;
+    const long long cols = (long long)sweep2_tiles_i(g->I) * ((g->J - 2 + S::R2 - 1) / S::R2);
+    const int sms = device_sm_count();
+    const int kd = sweep2_kdepth(cols, g->K - 2, sms);
+    const long long items = cols * ((g->K - 2 + kd - 1) / kd);
+    return kWsHeaderBytes + round_up((size_t)std::min<long long>(items, sms) * sizeof(double), 256);
+}
+
+jac_status sweep2_run(const jac_grid *g, int kdepth, int n_pass, double *d_residual, void *workspace,
+                      size_t ws_bytes, cudaStream_t st)
+{
+    using S = Sweep2Shape;
+    Sweep2Desc d;
+    std::memset(&d, 0, sizeof(d));
+    d.I = g->I; d.J = g->J; d.K = g->K;
+    d.pitch = jac_pitch(g->I);
+    d.nti = sweep2_tiles_i(g->I);
+    d.ntj = (g->J - 2 + S::R2 - 1) / S::R2;
+    const int sms = device_sm_count();
+    d.kdepth = kdepth > 0 ? kdepth : sweep2_kdepth((long)d.nti * d.ntj, g->K - 2, sms);
+    d.nkb = (g->K - 2 + d.kdepth - 1) / d.kdepth;
+    const long long items = (long long)d.nti * d.ntj * d.nkb;
+    if (items > 0x3fffffffLL) return fail2(JAC_EINVAL, "grid too large for the two-sweep launch shape");
+    d.nitems = (int)items;
+    d.p_buf[0] = g->p[0];
+    d.p_buf[1] = g->p[1];
+    jac_status s;
+    for (int b = 0; b < 2; ++b)
+        if ((s = encode_box_map(&d.p[b], g->p[b], 4, d.pitch, d.pitch, g->J, g->K, S::PW, S::PH)) != JAC_OK)
+            return s;
+    for (int q = JAC_A0; q <= JAC_BND; ++q)
+        if ((s = encode_box_map(&d.coef[q - 1], g->coef[q], 4, d.pitch, d.pitch, g->J, g->K, S::TI, S::R1)) !=
+            JAC_OK)
+            return s;
+    const unsigned nblocks = (unsigned)std::min<long long>(items, sms);
+    if (ws_bytes < kWsHeaderBytes + (size_t)nblocks * sizeof(double))
+        return fail2(JAC_EINVAL, "workspace too small for the two-sweep launch");
+    WsHeader *hdr = static_cast<WsHeader *>(workspace);
+    Sweep2Args a;
+    std::memset(&a, 0, sizeof(a));
+    a.n_pass = n_pass;
+    a.par = 0;
+    a.omega = g->omega;
+    a.partials = reinterpret_cast<double *>(static_cast<char *>(workspace) + kWsHeaderBytes);
+    a.res = d_residual;
+    a.hdr = hdr;
+    SweepArgs la;
+    std::memset(&la, 0, sizeof(la));
+    set_l2_policy(la, g->prec, (size_t)d.pitch * g->J * g->K);
+    a.l2_keep_state = la.l2_keep_state;
+    a.l2_keep_coef = la.l2_keep_coef;
+
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [] {
+        attr_err = cudaFuncSetAttribute(k_sweep2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+    });
+    if (attr_err != cudaSuccess)
+        return fail2(JAC_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(attr_err));
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(nblocks);
+    cfg.blockDim = dim3(S::THREADS);
+    cfg.dynamicSmemBytes = S::SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_sweep2, d, a);
+    if (e != cudaSuccess) return fail2(JAC_ECUDA, std::string("two-sweep launch: ") + cudaGetErrorString(e));
+    return JAC_OK;
+}
+
+}  // namespace jac

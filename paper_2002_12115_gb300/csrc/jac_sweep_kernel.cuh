@@ -103,6 +103,30 @@ __device__ __forceinline__ float a3s_minus_one(float a3, float a0, float a1, flo
     }
 }
 
+// ss of one point for FP32 arithmetic, in difference form: the coefficients
+// times (neighbour - centre), the three b brackets and wrk1, then
+// a3 * that + p (a3 S - 1) with a3 S - 1 exact; times bnd.  Shared by the
+// single-sweep and the two-sweep kernels, so that both round alike.
+template <bool EXACT_SUM>
+__device__ __forceinline__ float ss_f32(float c, float xp, float xm, float yp, float ym, float zp, float zm,
+                                        float bij, float bjk, float bik, float a0, float a1, float a2, float a3,
+                                        float b0, float b1, float b2, float c0, float c1, float c2, float wk,
+                                        float bnd)
+{
+    float d = wk;
+    d = fmaf(a0, xp - c, d);
+    d = fmaf(a1, yp - c, d);
+    d = fmaf(a2, zp - c, d);
+    d = fmaf(c0, xm - c, d);
+    d = fmaf(c1, ym - c, d);
+    d = fmaf(c2, zm - c, d);
+    d = fmaf(b0, bij, d);
+    d = fmaf(b1, bjk, d);
+    d = fmaf(b2, bik, d);
+    const float ec = a3s_minus_one<EXACT_SUM>(a3, a0, a1, a2, c0, c1, c2);
+    return fmaf(a3, d, c * ec) * bnd;
+}
+
 __device__ __forceinline__ void neumaier_add(double &s, double &c, double x)
 {
     const double t = s + x;
@@ -451,19 +475,9 @@ k_sweep(const __grid_constant__ GridDesc d0, const SweepArgs a)
                         T ss;
                         if constexpr (sizeof(T) == 4) {
                             // difference form with an exact a3*S - 1
-                            T d = cwk[e];
-                            d = fmaf(ca0[e], ek1[e + 2] - c, d);
-                            d = fmaf(ca1[e], ek2[e + 1] - c, d);
-                            d = fmaf(ca2[e], ep1[e + 1] - c, d);
-                            d = fmaf(cc0[e], ek1[e] - c, d);
-                            d = fmaf(cc1[e], ek0[e + 1] - c, d);
-                            d = fmaf(cc2[e], em1[e + 1] - c, d);
-                            d = fmaf(cb0[e], bij, d);
-                            d = fmaf(cb1[e], bjk, d);
-                            d = fmaf(cb2[e], bik, d);
-                            const T ec = a3s_minus_one<EXACT_SUM>(ca3[e], ca0[e], ca1[e], ca2[e], cc0[e], cc1[e],
-                                                                  cc2[e]);
-                            ss = fmaf(ca3[e], d, c * ec) * cbn[e];
+                            ss = ss_f32<EXACT_SUM>(c, ek1[e + 2], ek1[e], ek2[e + 1], ek0[e + 1], ep1[e + 1],
+                                                   em1[e + 1], bij, bjk, bik, ca0[e], ca1[e], ca2[e], ca3[e],
+                                                   cb0[e], cb1[e], cb2[e], cc0[e], cc1[e], cc2[e], cwk[e], cbn[e]);
                         } else {
                             // FP64: the written form, fused
                             T s0 = cwk[e];
