@@ -240,6 +240,26 @@ def oracle_sample(w: dict, min_seconds: float = 10.0, max_sweeps: int = 4000, ch
     return gpts, cores, sample
 
 
+def oracle_one_core(w: dict, seconds: float = 3.0, chunk: int = 2):
+    """The same oracle on one thread, for a few seconds: Gpt/s."""
+    import jacobi_inputs as ji
+    import oracle
+    cores = oracle.set_threads(0)
+    oracle.set_threads(1)
+    try:
+        f = ji.himeno_fields(w["I"], w["J"], w["K"])
+        p = f["p"]
+        done, t_total = 0, 0.0
+        while t_total < seconds:
+            t0 = time.perf_counter()
+            p, _ = oracle.run(f, chunk, 0.8, p0=p)
+            t_total += time.perf_counter() - t0
+            done += chunk
+    finally:
+        oracle.set_threads(cores)
+    return n_interior(w) * done / t_total / 1e9
+
+
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -639,7 +659,8 @@ def run_native(args, w, wname):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         gpts, cores, sample = oracle_sample(w, min_seconds=args.cpu_seconds)
-        cpu = {"value": gpts, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        cpu = {"value": gpts, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "value_one_core": oracle_one_core(w)}
     emit({
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
