@@ -362,15 +362,15 @@ jac_status validate_grid(const jac_grid *g)
     return JAC_OK;
 }
 
-template <typename T, typename C, int TJ, bool BATCH>
+template <typename T, typename C, int TJ, bool BATCH, bool DEEP = false>
 jac_status launch_sweep_kernel(const GridDesc &d0, const SweepArgs &a, unsigned nblocks, cudaStream_t st)
 {
-    using S = SweepShape<T, C, TJ>;
+    using S = SweepShape<T, C, TJ, DEEP>;
     static_assert(S::RC >= 2, "coefficient ring too shallow for the shared-memory budget");
     static std::once_flag attr_once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(attr_once, [] {
-        attr_err = cudaFuncSetAttribute(k_sweep<T, C, TJ, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        attr_err = cudaFuncSetAttribute(k_sweep<T, C, TJ, BATCH, DEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)S::SMEM);
     });
     if (attr_err != cudaSuccess) return cuda_fail(attr_err, "cudaFuncSetAttribute");
@@ -385,7 +385,7 @@ jac_status launch_sweep_kernel(const GridDesc &d0, const SweepArgs &a, unsigned 
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k_sweep<T, C, TJ, BATCH>, d0, a);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_sweep<T, C, TJ, BATCH, DEEP>, d0, a);
     if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
     return JAC_OK;
 }
@@ -401,7 +401,11 @@ jac_status launch_sweep(jac_prec prec, int tj, const GridDesc &d0, const SweepAr
         break;
     case JAC_F32:
         if (tj == 4) return launch_sweep_kernel<float, float, 4, BATCH>(d0, a, nblocks, st);
-        if (tj == 8) return launch_sweep_kernel<float, float, 8, BATCH>(d0, a, nblocks, st);
+        if (tj == 8) {
+            // a fourth coefficient stage when the state stays in L2
+            if (!BATCH && a.l2_keep_state) return launch_sweep_kernel<float, float, 8, false, true>(d0, a, nblocks, st);
+            return launch_sweep_kernel<float, float, 8, BATCH>(d0, a, nblocks, st);
+        }
         break;
     case JAC_F32_BF16COEF:
         if (tj == 4) return launch_sweep_kernel<float, __nv_bfloat16, 4, BATCH>(d0, a, nblocks, st);

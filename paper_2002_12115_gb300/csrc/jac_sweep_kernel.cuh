@@ -137,7 +137,11 @@ __device__ __forceinline__ void neumaier_add(double &s, double &c, double x)
 
 // Compile-time shape of a kernel instantiation: TJ consumer warps, VI points
 // per lane, row folds rw in {1, .., RW_MAX}.
-template <typename T, typename C, int TJ>
+// DEEP: the larger shared-memory budget, which gives FP32 with 8 consumer
+// warps a fourth coefficient stage; it pays where the state stays in L2
+// (more coefficient bytes in flight) and costs where the state streams from
+// DRAM (the deeper coefficient queue delays the state copies).
+template <typename T, typename C, int TJ, bool DEEP = false>
 struct SweepShape {
     static constexpr int VI = 16 / (int)sizeof(T);        // points per lane (16 bytes)
     static constexpr int TI = 32 * VI;                     // tile width at rw = 1
@@ -153,7 +157,7 @@ struct SweepShape {
     static constexpr int TILE_T = TI * TJ * (int)sizeof(T);
     static constexpr uint32_t C_TX = (uint32_t)(11 * TILE_C + TILE_T);
     static constexpr int C_STRIDE = (int)((C_TX + 127) / 128 * 128);
-    static constexpr int BUDGET = 220 * 1024;
+    static constexpr int BUDGET = (DEEP ? 226 : 220) * 1024;
     static constexpr int RC_FIT = (BUDGET - RP * P_STRIDE - 1024) / C_STRIDE;
     static constexpr int RC = RC_FIT > 8 ? 8 : RC_FIT;     // coefficient stages
     static constexpr size_t SMEM = (size_t)RP * P_STRIDE + (size_t)RC * C_STRIDE + 128;
@@ -259,11 +263,11 @@ __device__ __forceinline__ Item decode_item(const SweepArgs &a, const GridDesc *
     return it;
 }
 
-template <typename T, typename C, int TJ, bool BATCH>
-__global__ void __launch_bounds__(SweepShape<T, C, TJ>::THREADS, 1)
+template <typename T, typename C, int TJ, bool BATCH, bool DEEP = false>
+__global__ void __launch_bounds__(SweepShape<T, C, TJ, DEEP>::THREADS, 1)
 k_sweep(const __grid_constant__ GridDesc d0, const SweepArgs a)
 {
-    using S = SweepShape<T, C, TJ>;
+    using S = SweepShape<T, C, TJ, DEEP>;
     constexpr int VI = S::VI, H = S::H, RP = S::RP, RC = S::RC;
     constexpr bool EXACT_SUM = sizeof(C) == 2;
     extern __shared__ unsigned char dsm_raw[];
