@@ -1,5 +1,6 @@
 // Shared device helpers of libjac: storage element types, PTX wrappers for
-// mbarriers, TMA tensor copies and streaming loads, and bounded waits.
+// mbarriers, TMA tensor copies, L2 cache policies and cache-hinted stores, and
+// bounded waits.
 #pragma once
 
 #include <cuda.h>
@@ -71,12 +72,6 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Programmatic dependent launch: let the next kernel in the stream start its
-// prologue, and wait until the previous one has completed and its writes are
-// visible.
-__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
 // Wait for the phase with the given parity to complete; gives up after
 // kWaitLimitNs and returns false.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
@@ -100,11 +95,6 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
 // (TMA) accesses, in both directions.
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
-// Named barrier over `count` threads (id 1; id 0 is __syncthreads).
-__device__ __forceinline__ void named_barrier_sync(int id, int count)
-{
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
 
 // Wait until *p >= target (acquire); false after kWaitLimitNs.
 __device__ __forceinline__ bool wait_counter_bounded(const unsigned *p, unsigned target)
@@ -164,66 +154,6 @@ __device__ __forceinline__ void st_v2d_hint(double *p, double a, double b, uint6
     asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(p), "d"(a), "d"(b), "l"(policy)
                  : "memory");
 }
-
-// ---------------------------------------------------------------- loads
-// Streaming 16-byte / 8-byte loads of read-only data, not kept in L1.
-__device__ __forceinline__ float4 ld_stream_f4(const float *p)
-{
-    float4 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "l"(p));
-    return v;
-}
-
-__device__ __forceinline__ double2 ld_stream_d2(const double *p)
-{
-    double2 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
-    return v;
-}
-
-__device__ __forceinline__ uint2 ld_stream_u2(const void *p)
-{
-    uint2 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
-    return v;
-}
-
-// VI consecutive values of storage type C at p, converted to T.
-template <typename T, typename C, int VI>
-struct CoefLoad;
-
-template <>
-struct CoefLoad<float, float, 4> {
-    static __device__ __forceinline__ void run(const void *p, float (&o)[4])
-    {
-        float4 v = ld_stream_f4(static_cast<const float *>(p));
-        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
-    }
-};
-
-template <>
-struct CoefLoad<double, double, 2> {
-    static __device__ __forceinline__ void run(const void *p, double (&o)[2])
-    {
-        double2 v = ld_stream_d2(static_cast<const double *>(p));
-        o[0] = v.x; o[1] = v.y;
-    }
-};
-
-template <>
-struct CoefLoad<float, __nv_bfloat16, 4> {
-    // BF16 -> FP32 is exact: the BF16 bits are the high half of the FP32 word.
-    static __device__ __forceinline__ void run(const void *p, float (&o)[4])
-    {
-        uint2 v = ld_stream_u2(p);
-        o[0] = __uint_as_float(v.x << 16);
-        o[1] = __uint_as_float(v.x & 0xffff0000u);
-        o[2] = __uint_as_float(v.y << 16);
-        o[3] = __uint_as_float(v.y & 0xffff0000u);
-    }
-};
 
 // Storage element type of array `which` under precision `prec` (host side).
 inline size_t elem_bytes(jac_prec prec, int which)
