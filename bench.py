@@ -339,39 +339,51 @@ def bench_single(args, w, stream):
             "residual": gosa, "jac": jac, "dev": dev, "clocks": clk.summary()}
 
 
-def bench_e2e(args, w, jac, stream):
+def bench_e2e(args, w, jac, stream, want_residual):
     """The same step through the C ABI from pinned host FP64 buffers: every
-    step copies its thirteen inputs in, sweeps, reads the residual and copies
-    the state out, all inside the timed region.  Two contexts on two streams
-    take the steps in turn, so one step's host-to-device copies run on the
-    copy engine while the previous step's sweeps run on the SMs."""
+    step copies its thirteen inputs in, sweeps, and copies the state and the
+    residual out, all inside the timed region.  Two contexts on two streams
+    take the steps in turn: one step's host-to-device copies run on the copy
+    engine while the previous step's sweeps hold the SMs, and the previous
+    step's results are copied out while this step sweeps."""
+    import numpy as np
     import torch
 
     import jacobi_inputs as ji
     from paper_2002_12115_gb300 import Jacobi
     I, J, K, n = w["I"], w["J"], w["K"], w["sweeps"]
     fields = ji.himeno_fields(I, J, K)
+
+    def pinned(shape):
+        return torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+
     host = {}
     for k, v in fields.items():
-        t = torch.empty(v.shape, dtype=torch.float64, pin_memory=True)
-        t.numpy()[...] = v
-        host[k] = t.numpy()
-    p_host = [torch.empty((K, J, I), dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
+        host[k] = pinned(v.shape)
+        host[k][...] = v
+    p_host = [pinned((K, J, I)) for _ in range(2)]
+    res_host = [pinned((1,)) for _ in range(2)]
     stream2 = torch.cuda.Stream()
     jac2 = Jacobi(I, J, K, w["prec"], 0.8, stream2)
     if args.tile_j or args.kdepth or args.tile_i or args.fuse:
         jac2.set_plan(args.tile_j, args.kdepth, args.tile_i, args.fuse)
     ctxs = (jac, jac2)
+    residuals = []
 
     def run(steps):
         for k in range(steps):
-            ctxs[k % 2].upload(host)
-            ctxs[k % 2].sweep(n)
-            if k >= 1:                       # finish the previous step meanwhile
-                ctxs[(k - 1) % 2].residual()
-                ctxs[(k - 1) % 2].download(p_host[(k - 1) % 2])
-        ctxs[(steps - 1) % 2].residual()
-        ctxs[(steps - 1) % 2].download(p_host[(steps - 1) % 2])
+            cur, prev = ctxs[k % 2], ctxs[(k - 1) % 2]
+            cur.upload_async(host)
+            if k >= 1:                       # the previous step's results, behind its sweeps
+                prev.download_async(p_host[(k - 1) % 2], res_host[(k - 1) % 2])
+            cur.sweep(n)
+            if k >= 1:
+                prev.sync()
+                residuals.append(float(res_host[(k - 1) % 2][0]))
+        last = ctxs[(steps - 1) % 2]
+        last.download_async(p_host[(steps - 1) % 2], res_host[(steps - 1) % 2])
+        last.sync()
+        residuals.append(float(res_host[(steps - 1) % 2][0]))
 
     run(max(2, args.warmup // 2))
     torch.cuda.synchronize()
@@ -382,6 +394,12 @@ def bench_e2e(args, w, jac, stream):
     torch.cuda.synchronize()
     ms = (time.perf_counter() - t0) * 1e3
     jac2.close()
+    # same inputs and a bitwise-reproducible sweep: every step's residual is
+    # the same, and (host and device input generators) that of the
+    # device-resident run within the FP32 state's rounding
+    if len(set(residuals)) != 1 or not abs(residuals[0] - want_residual) <= 1e-5 * abs(want_residual):
+        raise RuntimeError(f"end-to-end residuals {sorted(set(residuals))} against the device-resident "
+                           f"run's {want_residual}")
     return ms, host
 
 
@@ -618,7 +636,7 @@ def run_native(args, w, wname):
     s = bench_single(args, w, stream)
     units = n_interior(w) * n * args.steps / 1e9
     value, ms = replica_value(units, s["ms"], world, args.dist)
-    e2e_ms, host = bench_e2e(args, w, s["jac"], stream)
+    e2e_ms, host = bench_e2e(args, w, s["jac"], stream, s["residual"])
     e2e, e2e_ms = replica_value(units, e2e_ms, world, args.dist)
 
     compare = {}

@@ -228,6 +228,18 @@ jac_status jac_set_plan(jac_ctx *ctx, const jac_plan *plan);
  * synchronously, and the call synchronises before returning). */
 jac_status jac_upload(jac_ctx *ctx, const jac_fields *host);
 
+/* Same as jac_upload without waiting: the thirteen host-to-device copies go
+ * into thirteen device staging arrays (13*I*J*K doubles, allocated by the
+ * first call and owned by the context), and the rounding kernels follow them
+ * on the stream, so the copies can run on the copy engine while another
+ * stream's sweeps hold the SMs.  The host arrays must stay unchanged until
+ * the stream has passed the copies (jac_sync); pinned arrays give
+ * asynchronous copies, pageable ones are copied by the driver before the
+ * call returns.  Synchronises when a tape is active (the tape is freed).
+ * Errors: as jac_upload, JAC_ENOMEM if the staging arrays cannot be
+ * allocated. */
+jac_status jac_upload_async(jac_ctx *ctx, const jac_fields *host);
+
 /* Same as jac_upload with the thirteen arrays in device memory (dense FP64);
  * asynchronous. */
 jac_status jac_upload_dev(jac_ctx *ctx, const jac_fields *dev);
@@ -246,6 +258,20 @@ jac_status jac_download(jac_ctx *ctx, double *p_host);
 
 /* Current state as dense FP64 into device memory (asynchronous). */
 jac_status jac_download_dev(jac_ctx *ctx, double *p_dev);
+
+/* jac_download and jac_residual without waiting: enqueues the copy of the
+ * current state (I*J*K doubles) to p_host and, if res_host is not NULL, of
+ * the residual of the last sweep to *res_host.  Both are valid once the
+ * stream has passed them (jac_sync); pinned destinations give asynchronous
+ * copies.  A device wait that gave up is reported by jac_sync.  Errors:
+ * JAC_EINVAL (NULL ctx or p_host), JAC_ESTATE (res_host given and no sweep
+ * since the last upload), JAC_ECUDA. */
+jac_status jac_download_async(jac_ctx *ctx, double *p_host, double *res_host);
+
+/* Wait for the context's stream and check the sweep workspace's error word:
+ * JAC_ETIMEOUT if a bounded device wait of an earlier sweep gave up (the
+ * word is cleared), JAC_ECUDA on a CUDA error. */
+jac_status jac_sync(jac_ctx *ctx);
 
 /* Sweeps completed since the last upload. */
 jac_status jac_sweep_count(const jac_ctx *ctx, long long *out);

@@ -66,6 +66,9 @@ _SIG = {
     "jac_set_plan": (_I, [_VP, ctypes.POINTER(jac_plan)]),
     "jac_upload": (_I, [_VP, ctypes.POINTER(jac_fields)]),
     "jac_upload_dev": (_I, [_VP, ctypes.POINTER(jac_fields)]),
+    "jac_upload_async": (_I, [_VP, ctypes.POINTER(jac_fields)]),
+    "jac_download_async": (_I, [_VP, _VP, _VP]),
+    "jac_sync": (_I, [_VP]),
     "jac_sweep": (_I, [_VP, _I]),
     "jac_residual": (_I, [_VP, ctypes.POINTER(ctypes.c_double)]),
     "jac_download": (_I, [_VP, _VP]),
@@ -156,6 +159,7 @@ class Jacobi:
         check(lib().jac_create(ctypes.byref(h), self.I, self.J, self.K, PRECS[prec], self.omega,
                                _VP(self.stream)))
         self._h = h
+        self._pending = []       # host arrays of asynchronous copies, until sync()
 
     # -- lifetime
     def close(self) -> None:
@@ -212,6 +216,31 @@ class Jacobi:
         """Same, from contiguous float64 CUDA tensors."""
         f = self._fields(fields, device=True)
         self._check(lib().jac_upload_dev(self._h, ctypes.byref(f)))
+
+    def upload_async(self, fields: dict) -> None:
+        """Copy in without waiting (pinned host arrays for an asynchronous
+        copy).  The arrays are kept referenced until sync()."""
+        f = self._fields(fields, device=False)
+        self._check(lib().jac_upload_async(self._h, ctypes.byref(f)))
+        self._pending.append(fields)
+
+    def download_async(self, out: np.ndarray, res_out: np.ndarray | None = None) -> None:
+        """Enqueue the copy-out of the state to `out` (float64, shape (K, J, I))
+        and, if given, of the residual to res_out[0] (a float64 array); both
+        are valid after sync()."""
+        if tuple(out.shape) != self.shape or out.dtype != np.float64 or not out.flags.c_contiguous:
+            raise ValueError(f"out: expected a contiguous float64 array of shape {self.shape}")
+        if res_out is not None and (res_out.dtype != np.float64 or res_out.size < 1):
+            raise ValueError("res_out: expected a float64 array of at least one element")
+        self._check(lib().jac_download_async(self._h, _VP(_host_ptr(out)),
+                                             _VP(_host_ptr(res_out)) if res_out is not None else None))
+        self._pending.append((out, res_out))
+
+    def sync(self) -> None:
+        """Wait for this context's stream; raises on a device wait that gave up."""
+        st = lib().jac_sync(self._h)
+        self._pending.clear()
+        self._check(st)
 
     def sweep(self, n: int) -> None:
         self._check(lib().jac_sweep(self._h, int(n)))

@@ -25,6 +25,7 @@ struct jac_ctx {
     void *pbuf[2] = {nullptr, nullptr};
     int cur = 0;                      // which pbuf holds the current state
     double *staging = nullptr;        // I*J*K doubles
+    double *stage_all = nullptr;      // JAC_NFIELDS*I*J*K doubles, jac_upload_async only (first use)
     void *ws = nullptr;               // sweep workspace
     size_t ws_bytes = 0;
     jac_plan plan{0, 0, 0, 0};
@@ -145,27 +146,50 @@ jac_status sweep_impl(jac_ctx *c, int n_iter)
     return JAC_OK;
 }
 
-jac_status upload_impl(jac_ctx *c, const jac_fields *f, bool on_device)
+enum class Src { host, device, host_async };
+
+// The copy-in.  Host sources go through device staging: one array reused
+// per field (synchronous), or, for the asynchronous form, one staging array
+// per field, so that all thirteen host-to-device copies run on the copy
+// engine without waiting for the packing kernels (which need free SMs).
+jac_status upload_impl(jac_ctx *c, const jac_fields *f, Src from)
 {
     if (!c) return ctx_fail(c, JAC_EINVAL, "ctx is NULL");
     if (!f) return ctx_fail(c, JAC_EINVAL, "fields is NULL");
     for (int q = 0; q < JAC_NFIELDS; ++q)
         if (!f->f[q]) return ctx_fail(c, JAC_EINVAL, "field " + std::to_string(q) + " is NULL");
     const size_t n = (size_t)c->I * c->J * c->K;
-    for (int q = 0; q < JAC_NFIELDS; ++q) {
-        const double *src = f->f[q];
-        if (!on_device) {
-            cudaError_t e = cudaMemcpyAsync(c->staging, src, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
-            if (e != cudaSuccess) return ctx_cuda(c, e, "host-to-device copy");
-            src = c->staging;
+    if (from == Src::host_async && !c->stage_all) {
+        cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&c->stage_all), JAC_NFIELDS * n * sizeof(double));
+        if (e != cudaSuccess) {
+            c->stage_all = nullptr;
+            return ctx_fail(c, JAC_ENOMEM, "device allocation of the asynchronous staging arrays failed");
         }
-        void *dst = (q == JAC_P) ? c->pbuf[0] : c->arr[q];
-        jac_status s = jac::pack_dev(c->I, c->J, c->K, c->prec, q, src, dst, c->stream);
+    }
+    const double *src[JAC_NFIELDS];
+    for (int q = 0; q < JAC_NFIELDS; ++q) {
+        src[q] = f->f[q];
+        if (from != Src::device) {
+            double *stage = (from == Src::host) ? c->staging : c->stage_all + (size_t)q * n;
+            cudaError_t e = cudaMemcpyAsync(stage, src[q], n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+            if (e != cudaSuccess) return ctx_cuda(c, e, "host-to-device copy");
+            src[q] = stage;
+        }
+        // one reused staging array: pack each field before the next copy
+        if (from == Src::host) {
+            jac_status s = jac::pack_dev(c->I, c->J, c->K, c->prec, q, src[q],
+                                         q == JAC_P ? c->pbuf[0] : c->arr[q], c->stream);
+            if (s != JAC_OK) return ctx_from_thread(c, s);
+        }
+    }
+    for (int q = 0; q < JAC_NFIELDS && from != Src::host; ++q) {
+        jac_status s = jac::pack_dev(c->I, c->J, c->K, c->prec, q, src[q], q == JAC_P ? c->pbuf[0] : c->arr[q],
+                                     c->stream);
         if (s != JAC_OK) return ctx_from_thread(c, s);
     }
     cudaError_t e = cudaMemcpyAsync(c->pbuf[1], c->pbuf[0], array_bytes(c, JAC_P), cudaMemcpyDeviceToDevice, c->stream);
     if (e != cudaSuccess) return ctx_cuda(c, e, "device copy of p0");
-    if (!on_device) {
+    if (from == Src::host) {
         e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) return ctx_cuda(c, e, "cudaStreamSynchronize");
     }
@@ -242,6 +266,7 @@ jac_status jac_destroy(jac_ctx *c)
     cudaStreamSynchronize(c->stream);
     if (c->ws) cudaFree(c->ws);
     if (c->staging) cudaFree(c->staging);
+    if (c->stage_all) cudaFree(c->stage_all);
     if (c->arena) cudaFree(c->arena);
     delete c;
     return JAC_OK;
@@ -266,9 +291,11 @@ jac_status jac_set_plan(jac_ctx *c, const jac_plan *plan)
     return ensure_workspace(c);
 }
 
-jac_status jac_upload(jac_ctx *c, const jac_fields *host) { return upload_impl(c, host, false); }
+jac_status jac_upload(jac_ctx *c, const jac_fields *host) { return upload_impl(c, host, Src::host); }
 
-jac_status jac_upload_dev(jac_ctx *c, const jac_fields *dev) { return upload_impl(c, dev, true); }
+jac_status jac_upload_async(jac_ctx *c, const jac_fields *host) { return upload_impl(c, host, Src::host_async); }
+
+jac_status jac_upload_dev(jac_ctx *c, const jac_fields *dev) { return upload_impl(c, dev, Src::device); }
 
 jac_status jac_sweep(jac_ctx *c, int n_iter)
 {
@@ -309,6 +336,29 @@ jac_status jac_download(jac_ctx *c, double *p_host)
     if (e != cudaSuccess) return ctx_cuda(c, e, "device-to-host copy");
     s = jac::workspace_check(c->ws, c->stream);  // synchronises
     return ctx_from_thread(c, s);
+}
+
+jac_status jac_download_async(jac_ctx *c, double *p_host, double *res_host)
+{
+    if (!c || !p_host) return ctx_fail(c, JAC_EINVAL, "NULL argument");
+    if (res_host && !c->has_res) return ctx_fail(c, JAC_ESTATE, "no sweep since the last upload");
+    jac_status s = jac_download_dev(c, c->staging);
+    if (s != JAC_OK) return s;
+    const size_t n = (size_t)c->I * c->J * c->K;
+    cudaError_t e = cudaMemcpyAsync(p_host, c->staging, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return ctx_cuda(c, e, "device-to-host copy");
+    if (res_host) {
+        jac::WsHeader *hdr = static_cast<jac::WsHeader *>(c->ws);
+        e = cudaMemcpyAsync(res_host, &hdr->residual, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return ctx_cuda(c, e, "residual copy");
+    }
+    return JAC_OK;
+}
+
+jac_status jac_sync(jac_ctx *c)
+{
+    if (!c) return ctx_fail(c, JAC_EINVAL, "ctx is NULL");
+    return ctx_from_thread(c, jac::workspace_check(c->ws, c->stream));
 }
 
 jac_status jac_sweep_count(const jac_ctx *c, long long *out)
@@ -417,7 +467,7 @@ jac_status jac_sweep_unhoisted(jac_ctx *c, int n_iter, const jac_fields *host, d
     jac_fields f = *host;
     f.f[JAC_P] = p_host;
     for (int t = 0; t < n_iter; ++t) {
-        jac_status s = upload_impl(c, &f, false);
+        jac_status s = upload_impl(c, &f, Src::host);
         if (s == JAC_OK) s = jac_sweep(c, 1);
         if (s == JAC_OK) s = jac_download(c, p_host);
         if (s != JAC_OK) return s;
