@@ -118,11 +118,17 @@ typedef struct jac_grid {
  * BF16 on grids a 128-wide tile covers fully), the tile width with the best
  * lane use, and a kdepth by precision: FP32/BF16 take the smallest depth
  * (at most 256) at which every work item of a sweep fits one round of CTAs,
- * else 8; FP64 minimises (work-item rounds per CTA) x (kdepth + 3).
+ * else 8; FP64 minimises (work-item rounds per CTA) x (kdepth + 3), or
+ * takes balanced ranges where their cost (planes per CTA + 3 per tile a
+ * range touches) is lower.  kdepth = JAC_KDEPTH_BALANCED: no fixed depth; with T tiles per plane and
+ * G CTAs, CTA b takes the tile-planes b*U/G .. (b+1)*U/G - 1 of the
+ * tile-major order of all U = T * (K - 2) tile-planes, one work item per
+ * tile that range touches, so every CTA gets the same number of planes.
  * Unsupported shapes: JAC_EINVAL at launch. */
+enum { JAC_KDEPTH_BALANCED = -1 };
 typedef struct jac_plan {
     int tile_j;   /* rows per work item */
-    int kdepth;   /* k-planes per work item, >= 1 */
+    int kdepth;   /* k-planes per work item, >= 1, or JAC_KDEPTH_BALANCED */
     int tile_i;   /* points per row */
     int fuse;     /* two sweeps per pass (FP32 storage only): 0 the library's
                      choice, which is single sweeps (on GB300 the two-sweep

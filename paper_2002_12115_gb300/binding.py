@@ -24,6 +24,8 @@ PRECS = {"f64": 0, "f32": 1, "bf16": 2}
 # array indices of a field set
 FIELDS = ("p", "a0", "a1", "a2", "a3", "b0", "b1", "b2", "c0", "c1", "c2", "wrk1", "bnd")
 NFIELDS = len(FIELDS)
+# jac_plan.kdepth: balanced ranges of tile-planes instead of a fixed depth
+KDEPTH_BALANCED = -1
 
 
 class JacError(RuntimeError):
