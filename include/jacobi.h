@@ -123,7 +123,9 @@ typedef struct jac_grid {
  * range touches) is lower.  kdepth = JAC_KDEPTH_BALANCED: no fixed depth; with T tiles per plane and
  * G CTAs, CTA b takes the tile-planes b*U/G .. (b+1)*U/G - 1 of the
  * tile-major order of all U = T * (K - 2) tile-planes, one work item per
- * tile that range touches, so every CTA gets the same number of planes.
+ * tile that range touches, so every CTA gets the same number of planes
+ * (FP64 storage only; with FP32 storage they measured slower than the
+ * rule above, and the call returns JAC_EINVAL).
  * Unsupported shapes: JAC_EINVAL at launch. */
 enum { JAC_KDEPTH_BALANCED = -1 };
 typedef struct jac_plan {

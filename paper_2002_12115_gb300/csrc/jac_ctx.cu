@@ -281,6 +281,8 @@ jac_status jac_set_plan(jac_ctx *c, const jac_plan *plan)
     if (plan) p = *plan;
     if (p.tile_j < 0 || p.tile_i < 0 || (p.kdepth < 0 && p.kdepth != JAC_KDEPTH_BALANCED))
         return ctx_fail(c, JAC_EINVAL, "negative plan entry");
+    if (p.kdepth == JAC_KDEPTH_BALANCED && c->prec != JAC_F64)
+        return ctx_fail(c, JAC_EINVAL, "balanced ranges (JAC_KDEPTH_BALANCED) are for FP64 storage");
     if (p.fuse < 0 || p.fuse > 2) return ctx_fail(c, JAC_EINVAL, "fuse must be 0, 1 or 2");
     if (p.tile_i || p.tile_j) {
         jac_grid g = make_grid(c);

@@ -311,6 +311,8 @@ jac_status check_plan(jac_prec prec, const jac_plan &p, int *rw_out, int *tj_out
                                     "BF16 coefficients and tile_i >= 32)");
     if (p.kdepth < 1 && p.kdepth != JAC_KDEPTH_BALANCED)
         return fail(JAC_EINVAL, "kdepth must be >= 1 or JAC_KDEPTH_BALANCED");
+    if (p.kdepth == JAC_KDEPTH_BALANCED && prec != JAC_F64)
+        return fail(JAC_EINVAL, "balanced ranges (JAC_KDEPTH_BALANCED) are for FP64 storage");
     *rw_out = rw;
     *tj_out = tj;
     return JAC_OK;
@@ -370,7 +372,7 @@ jac_status validate_grid(const jac_grid *g)
     return JAC_OK;
 }
 
-template <typename T, typename C, int TJ, bool BATCH, bool DEEP = false>
+template <typename T, typename C, int TJ, bool BATCH, bool DEEP = false, bool BAL = false>
 jac_status launch_sweep_kernel(const GridDesc &d0, const SweepArgs &a, unsigned nblocks, cudaStream_t st)
 {
     using S = SweepShape<T, C, TJ, DEEP>;
@@ -378,7 +380,7 @@ jac_status launch_sweep_kernel(const GridDesc &d0, const SweepArgs &a, unsigned 
     static std::once_flag attr_once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(attr_once, [] {
-        attr_err = cudaFuncSetAttribute(k_sweep<T, C, TJ, BATCH, DEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        attr_err = cudaFuncSetAttribute(k_sweep<T, C, TJ, BATCH, DEEP, BAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)S::SMEM);
     });
     if (attr_err != cudaSuccess) return cuda_fail(attr_err, "cudaFuncSetAttribute");
@@ -393,7 +395,7 @@ jac_status launch_sweep_kernel(const GridDesc &d0, const SweepArgs &a, unsigned 
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k_sweep<T, C, TJ, BATCH, DEEP>, d0, a);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_sweep<T, C, TJ, BATCH, DEEP, BAL>, d0, a);
     if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
     return JAC_OK;
 }
@@ -404,6 +406,11 @@ jac_status launch_sweep(jac_prec prec, int tj, const GridDesc &d0, const SweepAr
 {
     switch (prec) {
     case JAC_F64:
+        if (!BATCH && a.bal_units > 0) {
+            if (tj == 4) return launch_sweep_kernel<double, double, 4, false, false, true>(d0, a, nblocks, st);
+            if (tj == 8) return launch_sweep_kernel<double, double, 8, false, false, true>(d0, a, nblocks, st);
+            break;
+        }
         if (tj == 4) return launch_sweep_kernel<double, double, 4, BATCH>(d0, a, nblocks, st);
         if (tj == 8) return launch_sweep_kernel<double, double, 8, BATCH>(d0, a, nblocks, st);
         break;
@@ -491,9 +498,19 @@ jac_status sweep_dev(const jac_grid *g, const jac_plan *plan, int n_iter, double
     a.partials = reinterpret_cast<double *>(static_cast<char *>(workspace) + kWsHeaderBytes);
     a.res = d_residual ? d_residual : &hdr->residual;
     a.hdr = hdr;
-    if (p.kdepth == JAC_KDEPTH_BALANCED) a.bal_units = sweep_units(g, p);
-    set_l2_policy(a, g->prec, (size_t)d0.pitch * g->J * g->K);
     const unsigned nblocks = (unsigned)std::min<long long>(sweep_units(g, p), num_sms());
+    if (p.kdepth == JAC_KDEPTH_BALANCED) {
+        // item numbers b + n G for n below the most tiles one CTA's range touches
+        const long long U = sweep_units(g, p), G = nblocks, nk = g->K - 2;
+        long long most = 1;
+        for (long long b = 0; b < G; ++b) {
+            const long long u0 = b * U / G, u1 = (b + 1) * U / G;
+            if (u1 > u0) most = std::max(most, (u1 - 1) / nk - u0 / nk + 1);
+        }
+        a.bal_units = U;
+        a.nitems = (int)(G * most);
+    }
+    set_l2_policy(a, g->prec, (size_t)d0.pitch * g->J * g->K);
     return launch_sweep<false>(g->prec, tj, d0, a, nblocks, static_cast<cudaStream_t>(stream));
 }
 

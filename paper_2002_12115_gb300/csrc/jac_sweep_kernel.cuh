@@ -67,10 +67,10 @@ struct SweepArgs {
     double omega;
     double *partials;          // ngrids * gridDim.x
     double *res;               // residual of the last sweep per grid (NULL: none)
-    long long bal_units;       // single grid: > 0 = balanced ranges over this many tile-planes
     WsHeader *hdr;
     int l2_keep_state;         // 1: state copies/stores evict_last, coefficients evict_first
     unsigned l2_keep_coef;     // bit q (JAC_A0..JAC_BND): array q's copies evict_last too
+    long long bal_units;       // balanced ranges (BAL kernels): tile-planes of the grid
 };
 
 // Fast2Sum step (Dekker): hi + b = s + err exactly when |hi| >= |b|.
@@ -264,42 +264,44 @@ __device__ __forceinline__ Item decode_item(const SweepArgs &a, const GridDesc *
     return it;
 }
 
-// The n-th work item of this CTA, false past its last.  Uniform items: item
-// blockIdx.x + n * gridDim.x of the enumeration above.  Balanced ranges
-// (single grid, a.bal_units = U > 0 tile-planes, tile t = tj + ntj * ti
-// covering tile-planes t * (K-2) .. (t+1) * (K-2) - 1): CTA b takes the
-// tile-planes b U / G .. (b+1) U / G - 1, one item per tile they touch.
-template <bool BATCH>
-__device__ __forceinline__ bool next_item(const SweepArgs &a, const GridDesc *d0, int n, Item &it)
+// Balanced ranges (single grid, a.bal_units = U tile-planes; tile
+// t = tj + ntj * ti covers tile-planes t (K-2) .. (t+1) (K-2) - 1): CTA b
+// takes the tile-planes b U / G .. (b+1) U / G - 1, as one item per tile
+// they touch.  Its n-th such item has the number b + n G; numbers past its
+// last item are empty (nout = 0).
+__device__ __forceinline__ Item balanced_item(const SweepArgs &a, const GridDesc *d0, int item)
 {
-    if constexpr (!BATCH) {
-        if (a.bal_units > 0) {
-            const long long G = gridDim.x, b = blockIdx.x, U = a.bal_units;
-            const long long u0 = b * U / G, u1 = (b + 1) * U / G;
-            const long long nk = d0->K - 2;
-            const long long start = (n == 0) ? u0 : (u0 / nk + n) * nk;
-            if (start >= u1) return false;
-            const long long tile = start / nk;
-            const long long end = min(u1, (tile + 1) * nk);
-            it.D = d0;
-            it.g = 0;
-            it.i0 = (int)(tile / d0->ntj) * d0->ti;
-            it.j0 = 1 + (int)(tile % d0->ntj) * d0->rows;
-            it.kb = 1 + (int)(start - tile * nk);
-            it.nout = (int)(end - start);
-            return true;
-        }
-    }
-    const int item = blockIdx.x + n * (int)gridDim.x;
-    if (item >= a.nitems) return false;
-    it = decode_item<BATCH>(a, d0, item);
-    return true;
+    const long long G = gridDim.x, b = blockIdx.x, U = a.bal_units;
+    const long long u0 = b * U / G, u1 = (b + 1) * U / G;
+    const long long nk = d0->K - 2;
+    const int n = (item - (int)blockIdx.x) / (int)gridDim.x;
+    const long long start = (n == 0) ? u0 : (u0 / nk + n) * nk;
+    const long long tile = start / nk;
+    Item it;
+    it.D = d0;
+    it.g = 0;
+    it.i0 = (int)(tile / d0->ntj) * d0->ti;
+    it.j0 = 1 + (int)(tile % d0->ntj) * d0->rows;
+    it.kb = 1 + (int)(start - tile * nk);
+    it.nout = (start < u1) ? (int)(min(u1, (tile + 1) * nk) - start) : 0;
+    return it;
 }
 
-template <typename T, typename C, int TJ, bool BATCH, bool DEEP = false>
+template <bool BATCH, bool BAL>
+__device__ __forceinline__ Item get_item(const SweepArgs &a, const GridDesc *d0, int item)
+{
+    if constexpr (BAL) return balanced_item(a, d0, item);
+    else return decode_item<BATCH>(a, d0, item);
+}
+
+// BAL: work items from balanced ranges (single grid) instead of fixed-depth
+// items; a separate instantiation, so that the fixed-depth kernels are
+// compiled exactly as without it.
+template <typename T, typename C, int TJ, bool BATCH, bool DEEP = false, bool BAL = false>
 __global__ void __launch_bounds__(SweepShape<T, C, TJ, DEEP>::THREADS, 1)
 k_sweep(const __grid_constant__ GridDesc d0, const SweepArgs a)
 {
+    static_assert(!(BATCH && BAL), "balanced ranges are for single grids");
     using S = SweepShape<T, C, TJ, DEEP>;
     constexpr int VI = S::VI, H = S::H, RP = S::RP, RC = S::RC;
     constexpr bool EXACT_SUM = sizeof(C) == 2;
@@ -333,9 +335,9 @@ k_sweep(const __grid_constant__ GridDesc d0, const SweepArgs a)
             uint32_t cc = 0;
             bool ok = true;
             for (int t = 0; t < n_iter && ok; ++t)
-                for (int n = 0; ok; ++n) {
-                    Item it;
-                    if (!next_item<BATCH>(a, &d0, n, it)) break;
+                for (int item = blockIdx.x; item < a.nitems && ok; item += G) {
+                    const Item it = get_item<BATCH, BAL>(a, &d0, item);
+                    if (BAL && it.nout == 0) continue;
                     for (int m = 0; m < it.nout; ++m, ++cc) {
                         const uint32_t slot = cc % RC, use = cc / RC;
                         if (use > 0 && !mbar_wait_bounded(&c_empty[slot], (use - 1) & 1)) { ok = false; break; }
@@ -368,9 +370,9 @@ k_sweep(const __grid_constant__ GridDesc d0, const SweepArgs a)
                     fence_proxy_async_global();
                 }
                 const int rb = (t + a.par) & 1;
-                for (int n = 0; ok; ++n) {
-                    Item it;
-                    if (!next_item<BATCH>(a, &d0, n, it)) break;
+                for (int item = blockIdx.x; item < a.nitems && ok; item += G) {
+                    const Item it = get_item<BATCH, BAL>(a, &d0, item);
+                    if (BAL && it.nout == 0) continue;
                     const CUtensorMap *pm = rb ? &it.D->p[1] : &it.D->p[0];
                     const uint32_t tx = it.D->p_tx;
                     for (int q = 0; q < it.nout + 2; ++q, ++pc) {
@@ -434,9 +436,9 @@ k_sweep(const __grid_constant__ GridDesc d0, const SweepArgs a)
         for (int t = 0; t < n_iter && ok; ++t) {
             const bool res = (t == n_iter - 1) && (a.res != nullptr);
             const int wb = (t + 1 + a.par) & 1;
-            for (int n = 0; ok; ++n) {
-                Item it;
-                if (!next_item<BATCH>(a, &d0, n, it)) break;
+            for (int item = blockIdx.x; item < a.nitems && ok; item += G) {
+                const Item it = get_item<BATCH, BAL>(a, &d0, item);
+                if (BAL && it.nout == 0) continue;
                 const GridDesc *D = it.D;
                 if (res && it.g != g_open) {
                     if (g_open >= 0 && !flush(g_open)) { ok = false; break; }

@@ -29,10 +29,10 @@ def _built():
 SMALL = [((3, 3, 3), 1), ((4, 4, 4), 3), ((5, 6, 7), 7), ((17, 9, 11), 5), ((37, 11, 9), 4),
          ((130, 9, 12), 3), ((131, 10, 6), 2), ((67, 19, 23), 6), ((9, 40, 5), 2)]
 # (tile_j, kdepth, tile_i); tile_i 0 = the widest tile for that tile_j
-# kdepth -1: balanced ranges of tile-planes
-PLANS = {"f64": [None, (4, 1, 0), (8, 3, 0), (8, 1000, 0), (32, 2, 16), (8, -1, 0), (16, -1, 32)],
-         "f32": [None, (4, 1, 0), (8, 3, 0), (8, 1000, 0), (32, 2, 32), (64, 3, 16), (8, -1, 0), (4, -1, 0)],
-         "bf16": [None, (4, 1, 0), (16, 3, 0), (8, 1000, 0), (64, 2, 32), (16, -1, 0)]}
+# kdepth -1: balanced ranges of tile-planes (FP64)
+PLANS = {"f64": [None, (4, 1, 0), (8, 3, 0), (8, 1000, 0), (32, 2, 16), (8, -1, 0), (16, -1, 32), (4, -1, 0)],
+         "f32": [None, (4, 1, 0), (8, 3, 0), (8, 1000, 0), (32, 2, 32), (64, 3, 16)],
+         "bf16": [None, (4, 1, 0), (16, 3, 0), (8, 1000, 0), (64, 2, 32)]}
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
@@ -143,7 +143,10 @@ def test_bitwise_reproducible_and_plan_invariant_state(prec):
     p1, g1 = gpu_run(f, 13, prec)
     p2, g2 = gpu_run(f, 13, prec)
     assert np.array_equal(p1, p2) and g1 == g2
-    for plan in ((4, 2), (16 if prec == "bf16" else 8, 7), (32, 5, 16), (8, -1), (32, -1, 16)):
+    plans = [(4, 2), (16 if prec == "bf16" else 8, 7), (32, 5, 16)]
+    if prec == "f64":
+        plans += [(8, -1), (32, -1, 16), (8, 40)]
+    for plan in plans:
         p3, g3 = gpu_run(f, 13, prec, plan)
         assert np.array_equal(p1, p3)
         assert abs(g3 - g1) <= 1e-13 * g1
@@ -174,6 +177,8 @@ def test_api_errors():
             jac.set_plan(8, 0, 48)         # not a power of two
         with pytest.raises(JacError, match="JAC_EINVAL"):
             jac.set_plan(8, -2)            # -1 (balanced) is the only negative depth
+        with pytest.raises(JacError, match="JAC_EINVAL"):
+            jac.set_plan(8, -1)            # balanced ranges: FP64 storage only
         jac.set_plan(0, 0)
         with pytest.raises(JacError, match="JAC_EINVAL"):
             jac.sweep(-1)
