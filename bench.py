@@ -58,6 +58,7 @@ WORKLOADS = {
     "medium-bf16": dict(I=257, J=257, K=513, sweeps=100, prec="bf16"),
     "batch": dict(n_grids=512, sweeps=100, prec="f32"),
     "tuners": dict(n_grids=512, sweeps=100, prec="f32"),
+    "oracle-configs": dict(),
     "adjoint": dict(I=513, J=513, K=1025, sweeps=100, taped=20, C=5, prec="f32"),
     "adjoint-medium": dict(I=257, J=257, K=513, sweeps=40, taped=20, C=5, prec="f32"),
 }
@@ -258,6 +259,55 @@ def oracle_one_core(w: dict, seconds: float = 3.0, chunk: int = 2):
     finally:
         oracle.set_threads(cores)
     return n_interior(w) * done / t_total / 1e9
+
+
+def oracle_configs():
+    """The FP64 CPU oracle, as it stands, on every workload configuration, on
+    this host's cores: full runs where they take seconds, bounded samples
+    (stated) elsewhere.  Input generation is outside the timed calls."""
+    import jacobi_inputs as ji
+    import oracle
+    oracle.build()
+    cores = oracle.set_threads(0)
+    out = {}
+
+    def timed(fn):
+        t0 = time.perf_counter()
+        fn()
+        return time.perf_counter() - t0
+
+    def interior(I, J, K):
+        return (I - 2) * (J - 2) * (K - 2)
+
+    f = ji.himeno_fields(33, 33, 65)
+    dt = timed(lambda: oracle.run(f, 200, 0.8))
+    out["33x33x65 f64, 200 sweeps"] = {"seconds": dt, "gpts": interior(33, 33, 65) * 200 / dt / 1e9,
+                                       "sample": "full run"}
+    f = ji.himeno_fields(129, 129, 257)
+    dt = timed(lambda: oracle.run(f, 1000, 0.8))
+    out["129x129x257, 1000 sweeps"] = {"seconds": dt, "gpts": interior(129, 129, 257) * 1000 / dt / 1e9,
+                                       "sample": "full run"}
+    f = ji.himeno_fields(65, 65, 129)
+    tg = ji.target_field(65, 65, 129)
+    dt = timed(lambda: oracle.adjoint(f, 50, tg, 0.8))
+    out["65x65x129 f64 adjoint, T = 50"] = {"seconds": dt, "sample": "full run: 50 sweeps forward (all states "
+                                                                     "kept), 50 reverse-mode sweeps"}
+    dims = ji.batch_dims(512)[:64]
+    grids = [ji.himeno_fields(I, J, K, seed=42 + g) for g, (I, J, K) in enumerate(dims)]
+    dt = timed(lambda: [oracle.run(fg, 100, 0.8) for fg in grids])
+    pts = sum(interior(*d) for d in dims)
+    out["512 grids, 100 sweeps"] = {"seconds_sample": dt, "gpts": pts * 100 / dt / 1e9,
+                                    "sample": f"the first 64 of the 512 grids ({pts} interior points of "
+                                              "126,983,056), all 100 sweeps each"}
+    del grids
+    f = ji.himeno_fields(513, 513, 65)
+    dt = timed(lambda: oracle.run(f, 3, 0.8))
+    g = interior(513, 513, 65) * 3 / dt / 1e9
+    out["513x513x1025, 100 sweeps"] = {"gpts": g, "seconds_extrapolated": interior(513, 513, 1025) * 100 / g / 1e9,
+                                       "sample": "3 sweeps of a 513x513x65 slab (same i-j plane), extrapolated "
+                                                 "by interior point-updates"}
+    return {"metric": METRIC + " (FP64 CPU oracle, every configuration)", "unit": UNIT, "cores": cores,
+            "kind": "oracle", "configs": out}
 
 
 def run_reference(args, w):
@@ -720,6 +770,10 @@ def main():
                     help="batch plan search: cached coordinate descent or the genetic algorithm")
     ap.add_argument("--quick", action="store_true", help="skip the batched / adjoint / large comparisons")
     args = ap.parse_args()
+    if args.workload == "oracle-configs":       # host cores only, no GPU
+        if int(os.environ.get("RANK", "0")) == 0:
+            print(json.dumps(oracle_configs()), flush=True)
+        return
     w = dict(WORKLOADS[args.workload])
     if args.sweeps:
         w["sweeps"] = args.sweeps
