@@ -61,6 +61,7 @@ WORKLOADS = {
     "oracle-configs": dict(),
     "adjoint": dict(I=513, J=513, K=1025, sweeps=100, taped=20, C=5, prec="f32"),
     "adjoint-medium": dict(I=257, J=257, K=513, sweeps=40, taped=20, C=5, prec="f32"),
+    "adjoint-65": dict(I=65, J=65, K=129, sweeps=50, taped=50, C=10, prec="f64"),
 }
 
 
