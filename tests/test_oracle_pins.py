@@ -234,6 +234,37 @@ def test_one_sweep_derivative_in_wrk1(oracle_mod):
     assert np.abs((p2 - p1) - OMEGA * f["bnd"] * f["a3"] * d).max() < 1e-15
 
 
+def test_superposition_over_sweeps(oracle_mod):
+    """With wrk1 = 0 a sweep is linear in the state (faces included: they are
+    copied), so n sweeps of a p1 + b p2 equal a (n sweeps of p1) + b (n
+    sweeps of p2); and n sweeps are affine in wrk1, so the change that adding
+    w2 to wrk1 makes does not depend on the wrk1 it is added to.  A term
+    that is not linear in p (a constant, an |x|, a product of two states)
+    breaks the first; a wrk1 weighted by the state breaks the second."""
+    I, J, K, n = 8, 7, 9, 4
+    f = ji.himeno_fields(I, J, K, seed=21)
+    rng = np.random.default_rng(21)
+    f0 = dict(f)
+    f0["wrk1"] = np.zeros_like(f["wrk1"])
+    p1, p2 = rng.uniform(-1, 1, f["p"].shape), rng.uniform(-1, 1, f["p"].shape)
+    a, b = 0.7, -1.3
+    q1, _ = oracle_mod.run(f0, n, OMEGA, p0=p1)
+    q2, _ = oracle_mod.run(f0, n, OMEGA, p0=p2)
+    q12, _ = oracle_mod.run(f0, n, OMEGA, p0=a * p1 + b * p2)
+    assert np.abs(q12 - (a * q1 + b * q2)).max() < 1e-13
+    w1, w2 = rng.uniform(-1, 1, f["p"].shape), rng.uniform(-1, 1, f["p"].shape)
+
+    def with_wrk1(w):
+        g = dict(f)
+        g["wrk1"] = w
+        return oracle_mod.run(g, n, OMEGA)[0]
+
+    d_at_w1 = with_wrk1(w1 + w2) - with_wrk1(w1)
+    d_at_0 = with_wrk1(w2) - with_wrk1(np.zeros_like(w2))
+    assert np.abs(d_at_w1 - d_at_0).max() < 1e-13
+    assert np.abs(d_at_0).max() > 1e-2          # wrk1 does move the state
+
+
 def test_minimal_grid_single_point(oracle_mod):
     """3^3 has one interior point; its new value is an affine function of its
     18 neighbours with slopes a3*coef (sign of each b corner), checked by
