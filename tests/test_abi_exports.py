@@ -55,3 +55,22 @@ def test_binding_loads_and_rejects_bad_arguments_without_gpu():
     g = pkg.jac_grid()
     n = ctypes.c_size_t()
     assert L.jac_sweep_workspace_size(ctypes.byref(g), None, ctypes.byref(n)) == 1
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/jacobi.h is a C header: it compiles as strict C99 (no torch or
+    C++ types in the boundary) and its plan constant has the documented value."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "jacobi.h"\n'
+                   "int main(void) { jac_plan p = {8, JAC_KDEPTH_BALANCED, 0, 0};\n"
+                   "  jac_fields f; (void)f; return p.kdepth == -1 && JAC_NOALLOC_MAX_CTAS == 2048 ? 0 : 1; }\n")
+    exe = tmp_path / "use_header"
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    assert subprocess.run([str(exe)]).returncode == 0
