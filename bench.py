@@ -57,11 +57,13 @@ WORKLOADS = {
     "medium": dict(I=257, J=257, K=513, sweeps=100, prec="f32"),
     "medium-bf16": dict(I=257, J=257, K=513, sweeps=100, prec="bf16"),
     "batch": dict(n_grids=512, sweeps=100, prec="f32"),
+    "batch-f64": dict(n_grids=512, sweeps=100, prec="f64"),
     "tuners": dict(n_grids=512, sweeps=100, prec="f32"),
     "oracle-configs": dict(),
     "adjoint": dict(I=513, J=513, K=1025, sweeps=100, taped=20, C=5, prec="f32"),
     "adjoint-medium": dict(I=257, J=257, K=513, sweeps=40, taped=20, C=5, prec="f32"),
     "adjoint-65": dict(I=65, J=65, K=129, sweeps=50, taped=50, C=10, prec="f64"),
+    "adjoint-f64": dict(I=513, J=513, K=1025, sweeps=100, taped=20, C=5, prec="f64"),
 }
 
 
@@ -493,20 +495,21 @@ def bench_variant(w, prec, dev, stream, sweeps):
             "gbs": gbs, "grid": [w["I"], w["J"], w["K"]], "prec": prec, "roofline": roofline}
 
 
-def bench_batch(args, stream, sweeps=100, steps=3, autotune=True, loops=True, tuner="cd"):
+def bench_batch(args, stream, sweeps=100, steps=3, autotune=True, loops=True, tuner="cd", prec="f32"):
     """512 grids, dims drawn from {17, .., 129}: one graph-replayed persistent
-    launch per step against loops of per-grid launches."""
+    launch per step against loops of per-grid launches.  The plan search runs
+    for FP32 storage; other precisions take the library's default plan."""
     import torch
 
     import jacobi_inputs as ji
     from paper_2002_12115_gb300 import JacobiBatch
     dims = ji.batch_dims(512)
     npts = sum((I - 2) * (J - 2) * (K - 2) for I, J, K in dims)
-    b = JacobiBatch(dims, "f32", 0.8, stream)
+    b = JacobiBatch(dims, prec, 0.8, stream)
     for g, (I, J, K) in enumerate(dims):
         b.upload_tensors(g, ji.himeno_fields_torch(I, J, K, seed=42 + g))
     plan = None
-    if autotune:
+    if autotune and prec == "f32":
         from paper_2002_12115_gb300 import autotune as at
         if tuner == "ga":
             plan = at.ga_tune_batch(b, M=10, T=10, n_sweeps=10, reps=2)
@@ -523,7 +526,7 @@ def bench_batch(args, stream, sweeps=100, steps=3, autotune=True, loops=True, tu
     ms = a.elapsed_time(e) / steps
     out = {"value": npts * sweeps / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
            "grids": len(dims), "points": npts, "sweeps": sweeps,
-           "gbs": BYTES_PER_POINT["f32"] * npts * sweeps / (ms * 1e-3) / 1e9,
+           "gbs": BYTES_PER_POINT[prec] * npts * sweeps / (ms * 1e-3) / 1e9,
            "launches_per_step": 1, "plan": plan, "info": b.info()}
     if loops:
         for key, per_sweep, launches in (("per_grid_launches", False, len(dims)),
@@ -649,19 +652,19 @@ def run_native(args, w, wname):
             args.dist.barrier()
             args.dist.destroy_process_group()
 
-    if wname == "batch":
+    if wname in ("batch", "batch-f64"):
         r = bench_batch(args, stream, sweeps=w["sweeps"], steps=args.steps, autotune=not args.no_autotune,
-                        tuner=args.tuner)
+                        tuner=args.tuner, prec=w["prec"])
         value, ms = replica_value(r["points"] * r["sweeps"] / 1e9, r["ms_per_step"], world, args.dist)
         return emit({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                      "warmup": 2, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                     "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                     "config": {"workload": "512 grids, dims drawn from {17,33,49,65,97,129}, f32, 100 sweeps "
-                                            "per step in one graph-replayed persistent launch",
-                                "l2": "inputs larger than L2 (7.9 GB swept per sweep)"},
-                     "roofline": {"bound": "hbm", "achieved": r["gbs"], "peak": peak, "unit": "GB/s",
-                                  "frac": r["gbs"] / peak, "peak_kind": peak_kind, "traffic": None,
-                                  "kernel": "k_sweep (batched)"},
+                     "vs_baseline": None, "dtype": DTYPE[w["prec"]], "data": "synthetic",
+                     "config": {"workload": f"512 grids, dims drawn from {{17,33,49,65,97,129}}, {w['prec']}, 100 "
+                                            "sweeps per step in one graph-replayed persistent launch",
+                                "l2": f"inputs larger than L2 ({BYTES_PER_POINT[w['prec']] * r['points'] / 1e9:.1f} GB "
+                                      "of interior-point bytes swept per sweep)"},
+                     "roofline": dict(variant_roofline(w["prec"], r["value"]), traffic=None,
+                                      kernel="k_sweep (batched)"),
                      "batch": r, "gpu_launches": args.steps})
     if wname == "tuners":
         r = bench_tuners(stream, sweeps=w["sweeps"])
