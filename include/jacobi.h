@@ -143,6 +143,14 @@ typedef struct jac_plan {
                      an even number of passes. */
 } jac_plan;
 
+/* The plan a sweep of this grid would run with on a device of sm_count SMs
+ * (one CTA per SM; sm_count <= 0: the current device's count): the zero
+ * fields of *plan (NULL: all zero) filled in by the rules above.  Only the
+ * dimensions and the precision of *g are read; no device memory is touched,
+ * and with sm_count > 0 no GPU is needed.  Errors: JAC_EINVAL for bad
+ * dimensions, precision or plan entries, or a shape the kernels lack. */
+jac_status jac_resolve_plan(const jac_grid *g, const jac_plan *plan, int sm_count, jac_plan *out);
+
 /* Bytes of device workspace jac_sweep_dev needs for this grid and plan. */
 jac_status jac_sweep_workspace_size(const jac_grid *g, const jac_plan *plan, size_t *bytes);
 

@@ -59,6 +59,7 @@ _SIG = {
     "jac_sweep_dev": (_I, [ctypes.POINTER(jac_grid), ctypes.POINTER(jac_plan), _I, _VP, _VP,
                            ctypes.c_size_t, _VP]),
     "jac_workspace_check": (_I, [_VP, _VP]),
+    "jac_resolve_plan": (_I, [ctypes.POINTER(jac_grid), ctypes.POINTER(jac_plan), _I, ctypes.POINTER(jac_plan)]),
     "jac_sweep_dev_noalloc": (_I, [ctypes.POINTER(jac_grid), ctypes.POINTER(jac_plan), _I, _VP, _VP]),
     "jac_pack_dev": (_I, [_I, _I, _I, _I, _I, _VP, _VP, _VP]),
     "jac_unpack_dev": (_I, [_I, _I, _I, _I, _I, _VP, _VP, _VP]),
@@ -314,6 +315,19 @@ class Jacobi:
         """Per-sweep copy-in / copy-out (measurement contrast only)."""
         f = self._fields(fields, device=False)
         self._check(lib().jac_sweep_unhoisted(self._h, int(n), ctypes.byref(f), _VP(_host_ptr(p_host))))
+
+
+def resolve_plan(I: int, J: int, K: int, prec: str = "f32", sm_count: int = 0, tile_j: int = 0, kdepth: int = 0,
+                 tile_i: int = 0, fuse: int = 0) -> dict:
+    """The launch plan a sweep of an I x J x K grid runs with on a device of
+    sm_count SMs (0: the current device); the zero entries are filled in."""
+    g = jac_grid()
+    g.I, g.J, g.K, g.prec, g.omega = int(I), int(J), int(K), PRECS[prec], 0.8
+    out = jac_plan()
+    check(lib().jac_resolve_plan(ctypes.byref(g), ctypes.byref(jac_plan(int(tile_j), int(kdepth), int(tile_i),
+                                                                        int(fuse))), int(sm_count),
+                                 ctypes.byref(out)))
+    return {"tile_j": out.tile_j, "kdepth": out.kdepth, "tile_i": out.tile_i, "fuse": out.fuse}
 
 
 def workspace_size(grid: jac_grid, tile_j: int = 0, kdepth: int = 0, tile_i: int = 0, fuse: int = 0) -> int:

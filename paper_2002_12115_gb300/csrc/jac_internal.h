@@ -18,6 +18,7 @@ void set_thread_error(const std::string &m);
 
 jac_status validate_grid(const jac_grid *g);
 jac_plan resolve_plan(const jac_grid *g, const jac_plan *plan);
+jac_plan resolve_plan_sms(const jac_grid *g, const jac_plan *plan, int sms);
 size_t sweep_workspace_bytes(const jac_grid *g, const jac_plan &p);
 jac_status sweep_dev(const jac_grid *g, const jac_plan *plan, int n_iter, double *d_residual, void *workspace,
                      size_t ws_bytes, void *stream);

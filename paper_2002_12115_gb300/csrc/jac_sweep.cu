@@ -260,7 +260,10 @@ int default_kdepth(long cols, int nk, int ctas, jac_prec prec)
     return bal_cost < best_cost ? JAC_KDEPTH_BALANCED : best;
 }
 
-jac_plan resolve_plan(const jac_grid *g, const jac_plan *plan)
+jac_plan resolve_plan(const jac_grid *g, const jac_plan *plan) { return resolve_plan_sms(g, plan, num_sms()); }
+
+// The plan of a grid for a device of `sms` SMs (one CTA per SM).
+jac_plan resolve_plan_sms(const jac_grid *g, const jac_plan *plan, int sms)
 {
     // defaults: 8 consumer warps (16 for BF16 coefficients on wide grids),
     // the tile width with the best lane use, kdepth from default_kdepth
@@ -289,7 +292,7 @@ jac_plan resolve_plan(const jac_grid *g, const jac_plan *plan)
     if (p.kdepth == 0) {
         const int ti = std::max(p.tile_i, 1), rows = std::max(p.tile_j, 1);
         const long cols = (long)((g->I - 2) / ti + 1) * ((g->J - 2 + rows - 1) / rows);
-        p.kdepth = default_kdepth(cols, g->K - 2, num_sms(), g->prec);
+        p.kdepth = default_kdepth(cols, g->K - 2, sms, g->prec);
     }
     return p;
 }
@@ -589,6 +592,23 @@ jac_status jac_sweep_dev(const jac_grid *g, const jac_plan *plan, int n_iter, do
                          size_t ws_bytes, void *stream)
 {
     return jac::sweep_dev(g, plan, n_iter, d_residual, workspace, ws_bytes, stream);
+}
+
+jac_status jac_resolve_plan(const jac_grid *g, const jac_plan *plan, int sm_count, jac_plan *out)
+{
+    if (!g || !out) return jac::fail(JAC_EINVAL, "NULL argument");
+    if (g->I < 3 || g->J < 3 || g->K < 3) return jac::fail(JAC_EINVAL, "every grid dimension must be >= 3");
+    if (g->prec != JAC_F64 && g->prec != JAC_F32 && g->prec != JAC_F32_BF16COEF)
+        return jac::fail(JAC_EINVAL, "unknown precision");
+    if (plan && (plan->tile_j < 0 || plan->tile_i < 0 || plan->fuse < 0 || plan->fuse > 2 ||
+                 (plan->kdepth < 0 && plan->kdepth != JAC_KDEPTH_BALANCED)))
+        return jac::fail(JAC_EINVAL, "bad plan entry");
+    const jac_plan p = jac::resolve_plan_sms(g, plan, sm_count > 0 ? sm_count : jac::device_sm_count());
+    int rw = 0, tj = 0;
+    jac_status s = jac::check_plan(g->prec, p, &rw, &tj);
+    if (s != JAC_OK) return s;
+    *out = p;
+    return JAC_OK;
 }
 
 jac_status jac_workspace_check(void *workspace, void *stream)
