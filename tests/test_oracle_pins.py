@@ -386,3 +386,29 @@ def test_adjoint_dot_product_identity(oracle_mod):
     lhs = np.sum(0.5 * (pp - pm) * lam)
     rhs = np.sum(dp * adj["g_p0"]) + np.sum(dw * adj["g_wrk1"])
     assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + np.sum(np.abs(dp * adj["g_p0"])))
+
+
+@pytest.mark.parametrize("state", ["f64", "f32"])
+def test_sampled_points_equal_the_full_run(oracle_mod, state):
+    """sample_after (each point from the oracle on the sub-box of radius n
+    around it, the form the full-size GPU tests use) gives, bitwise, the full
+    run's value: after n sweeps a point depends only on points within
+    Chebyshev distance n, and the sub-box's held faces reach the centre only
+    at sweep n + 1.  Points near the grid faces clip the box to the grid."""
+    I, J, K, n = 21, 17, 15, 4
+    f = ji.himeno_fields(I, J, K, seed=31)
+    if state == "f32":
+        f = oracle_mod.round_inputs(f, "f32")
+    full, _ = oracle_mod.run(f, n, OMEGA, state=state)
+    pts = [(10, 8, 7), (1, 1, 1), (I - 2, J - 2, K - 2), (5, 12, 2), (15, 3, 11)]
+    got = oracle_mod.sample_after(f, n, pts, OMEGA, state=state)
+    want = np.array([full[k, j, i] for i, j, k in pts])
+    assert np.array_equal(got, want)
+    # the radius is tight: a box of radius n - 1 holds faces that reach the
+    # centre within n sweeps, and the value differs
+    i, j, k = pts[0]
+    r = n - 1
+    sub = {name: np.ascontiguousarray(v[k - r:k + r + 1, j - r:j + r + 1, i - r:i + r + 1])
+           for name, v in f.items()}
+    p_small, _ = oracle_mod.run(sub, n, OMEGA, state=state)
+    assert p_small[r, r, r] != full[k, j, i]
