@@ -12,9 +12,9 @@ include/jacobi.h, with hand-written sm_103a CUDA kernels.
         gosa = jac.residual()     # residual of the last sweep
         p = jac.download()        # one copy-out
 """
-from .binding import (FIELDS, PRECS, JacError, Jacobi, JacobiBatch, adjoint_step_dev, check, jac_fields, jac_grid,
-                      jac_plan, lib, pack_dev, pitch, stream_handle, sweep_dev, unpack_dev, workspace_check,
-                      workspace_size)
+from .binding import (FIELDS, KDEPTH_BALANCED, PRECS, JacError, Jacobi, JacobiBatch, adjoint_step_dev, check,
+                      jac_fields, jac_grid, jac_plan, lib, pack_dev, pitch, resolve_plan, stream_handle, sweep_dev,
+                      unpack_dev, workspace_check, workspace_size)
 
 
 def __getattr__(name):
@@ -25,6 +25,6 @@ def __getattr__(name):
     raise AttributeError(name)
 
 
-__all__ = ["FIELDS", "PRECS", "JacError", "Jacobi", "JacobiBatch", "JacobiSweep", "adjoint_step_dev", "check",
-           "jac_fields", "jac_grid", "jac_plan", "jacobi_sweep", "lib", "pack_dev", "pitch", "stream_handle",
-           "sweep_dev", "unpack_dev", "workspace_check", "workspace_size"]
+__all__ = ["FIELDS", "KDEPTH_BALANCED", "PRECS", "JacError", "Jacobi", "JacobiBatch", "JacobiSweep",
+           "adjoint_step_dev", "check", "jac_fields", "jac_grid", "jac_plan", "jacobi_sweep", "lib", "pack_dev",
+           "pitch", "resolve_plan", "stream_handle", "sweep_dev", "unpack_dev", "workspace_check", "workspace_size"]
