@@ -265,6 +265,49 @@ def test_superposition_over_sweeps(oracle_mod):
     assert np.abs(d_at_0).max() > 1e-2          # wrk1 does move the state
 
 
+def _longhand_point(P, f, i, j, k):
+    """One point's update written out term by term from the workload's
+    definition of the stencil (arrays indexed [k, j, i])."""
+    a0, a1, a2, a3 = f["a0"][k, j, i], f["a1"][k, j, i], f["a2"][k, j, i], f["a3"][k, j, i]
+    b0, b1, b2 = f["b0"][k, j, i], f["b1"][k, j, i], f["b2"][k, j, i]
+    c0, c1, c2 = f["c0"][k, j, i], f["c1"][k, j, i], f["c2"][k, j, i]
+    s0 = (a0 * P[k, j, i + 1] + a1 * P[k, j + 1, i] + a2 * P[k + 1, j, i]
+          + b0 * (P[k, j + 1, i + 1] - P[k, j - 1, i + 1] - P[k, j + 1, i - 1] + P[k, j - 1, i - 1])
+          + b1 * (P[k + 1, j + 1, i] - P[k - 1, j + 1, i] - P[k + 1, j - 1, i] + P[k - 1, j - 1, i])
+          + b2 * (P[k + 1, j, i + 1] - P[k - 1, j, i + 1] - P[k + 1, j, i - 1] + P[k - 1, j, i - 1])
+          + c0 * P[k, j, i - 1] + c1 * P[k, j - 1, i] + c2 * P[k - 1, j, i]
+          + f["wrk1"][k, j, i])
+    ss = (s0 * a3 - P[k, j, i]) * f["bnd"][k, j, i]
+    return P[k, j, i] + OMEGA * ss, ss
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_brute_force_4cubed_longhand(oracle_mod, n):
+    """4^3 (eight interior points), one to three Jacobi sweeps: every point's
+    19 terms written out by hand from the stencil's definition, each sweep
+    reading only the previous state, the faces never written, and the
+    residual the sum of the last sweep's ss^2.  One interior point is masked
+    (bnd = 0).  Agreement to rounding of the same operations."""
+    f = ji.himeno_fields(4, 4, 4, seed=41)
+    f["bnd"] = f["bnd"].copy()
+    f["bnd"][2, 1, 2] = 0.0
+    P = f["p"].copy()
+    for _ in range(n):
+        new = P.copy()
+        sq = []
+        for k in (1, 2):
+            for j in (1, 2):
+                for i in (1, 2):
+                    new[k, j, i], ss = _longhand_point(P, f, i, j, k)
+                    sq.append(ss * ss)
+        P = new
+    gosa = float(np.sum(sq))
+    got_p, got_g = oracle_mod.run(f, n, OMEGA)
+    assert np.abs(got_p - P).max() <= 1e-15 * np.abs(P).max()
+    assert abs(got_g - gosa) <= 1e-14 * gosa
+    assert got_p[2, 1, 2] == f["p"][2, 1, 2]
+
+
 def test_minimal_grid_single_point(oracle_mod):
     """3^3 has one interior point; its new value is an affine function of its
     18 neighbours with slopes a3*coef (sign of each b corner), checked by
