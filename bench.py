@@ -495,6 +495,21 @@ def bench_variant(w, prec, dev, stream, sweeps):
             "gbs": gbs, "grid": [w["I"], w["J"], w["K"]], "prec": prec, "roofline": roofline}
 
 
+def residual_vs_f64(w, dev, stream, sweeps):
+    """The residual after `sweeps` FP32 sweeps against the FP64 GPU run of the
+    same grid from the same inputs (relative): the FP32 state's error on the
+    observable the method reports."""
+    from paper_2002_12115_gb300 import Jacobi
+    res = {}
+    for vp in ("f32", "f64"):
+        with Jacobi(w["I"], w["J"], w["K"], vp, 0.8, stream) as vj:
+            vj.upload_tensors(dev)
+            vj.sweep(sweeps)
+            res[vp] = vj.residual()
+    return {"sweeps": sweeps, "gosa_f32": res["f32"], "gosa_f64": res["f64"],
+            "rel_err": abs(res["f32"] - res["f64"]) / abs(res["f64"])}
+
+
 def bench_batch(args, stream, sweeps=100, steps=3, autotune=True, loops=True, tuner="cd", prec="f32"):
     """512 grids, dims drawn from {17, .., 129}: one graph-replayed persistent
     launch per step against loops of per-grid launches.  The plan search runs
@@ -712,6 +727,11 @@ def run_native(args, w, wname):
         big = device_fields(513, 513, 1025)
         for vp in ("f32", "bf16", "f64"):
             compare["large_" + vp] = bench_variant(WORKLOADS["large"], vp, big, stream, 30 if vp == "f64" else 50)
+        try:   # a reported comparison, not a timed figure: an error here is recorded, not raised
+            compare["large_f32"]["residual_vs_f64"] = residual_vs_f64(WORKLOADS["large"], big, stream,
+                                                                      WORKLOADS["large"]["sweeps"])
+        except Exception as e:  # noqa: BLE001
+            compare["large_f32"]["residual_vs_f64"] = {"error": str(e)}
         del big
         torch.cuda.empty_cache()
 
