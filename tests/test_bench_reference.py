@@ -1,0 +1,41 @@
+"""The benchmark's reference arm (`bench.py --impl reference`: the FP64 CPU
+oracle timed on the host cores) and its host-only oracle-timing line run
+without a GPU and print one JSON line with the keys the benchmark contract
+names."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def run_bench(*args, timeout=600):
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], capture_output=True, text=True,
+                       timeout=timeout, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1, r.stdout
+    return json.loads(lines[0])
+
+
+def test_reference_arm_line():
+    d = run_bench("--impl", "reference", "--steps", "1", "--warmup", "0")
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    assert d["config"]["grid"] == [129, 129, 257]
+
+
+@pytest.mark.slow
+def test_oracle_configs_line():
+    d = run_bench("--workload", "oracle-configs")
+    assert d["kind"] == "oracle" and d["cores"] >= 1
+    assert len(d["configs"]) == 5
+    for name, c in d["configs"].items():
+        assert "sample" in c, name
