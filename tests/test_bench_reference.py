@@ -39,3 +39,19 @@ def test_oracle_configs_line():
     assert len(d["configs"]) == 5
     for name, c in d["configs"].items():
         assert "sample" in c, name
+
+
+def test_native_arm_has_no_cpu_fallback():
+    """Without a GPU the native arm fails loudly instead of printing a number,
+    and the binding refuses to create a context."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--steps", "1", "--warmup", "0",
+                        "--quick", "--no-variants", "--no-cpu-baseline"], capture_output=True, text=True,
+                       timeout=300, cwd=ROOT)
+    assert r.returncode != 0
+    assert not any(ln.lstrip().startswith("{") for ln in r.stdout.splitlines())
+    from paper_2002_12115_gb300 import Jacobi
+    with pytest.raises(Exception):
+        Jacobi(9, 9, 9, "f32")
