@@ -155,8 +155,11 @@ jac_status jac_resolve_plan(const jac_grid *g, const jac_plan *plan, int sm_coun
 jac_status jac_sweep_workspace_size(const jac_grid *g, const jac_plan *plan, size_t *bytes);
 
 /* n_iter sweeps of grid g on the given stream (a cudaStream_t, NULL for the
- * legacy default stream).  If d_residual is not NULL, the residual of the
- * last sweep is written there (one double, device memory).  workspace: device
+ * legacy default stream): the Himeno relaxation loop of Section 5.1.1 on
+ * arrays already present on the device (Section 3.3).  If d_residual is not
+ * NULL, the residual of the last sweep is written there (one double, device
+ * memory); if a bounded device wait gave up, that residual is NaN and the
+ * workspace's error word is set (jac_workspace_check).  workspace: device
  * memory of at least jac_sweep_workspace_size bytes, 16-byte aligned; its
  * first 256 bytes must be zero before the first call that uses it (the
  * kernels leave them zero again).  Calls that share a workspace must not
@@ -198,16 +201,21 @@ jac_status jac_unpack_dev(int I, int J, int K, jac_prec prec, int which,
  * allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
  *   - The first call on a device looks up that array's device address
  *     (cudaGetSymbolAddress, with the device current); make that first call
- *     before any stream capture on the device.
+ *     before any stream capture on the device.  The address is kept for the
+ *     life of the process: after cudaDeviceReset (which unloads the
+ *     library's device memory) do not call this entry point again on that
+ *     device in the same process.
  *   - Every call shares the array and overwrites what the previous call left
  *     there; its header is cleared (cudaMemsetAsync) at the start of each
  *     call.  Calls that overlap on the GPU (other streams, other host threads)
  *     race on it: serialise them.
  *   - Pass d_residual (device memory) to receive the residual; with NULL it
  *     lands in the shared array and is lost to the next call.
- *   - A bounded device wait that gives up is recorded only in the shared
- *     array and is not reported; callers who need that report use
- *     jac_sweep_dev with their own workspace and jac_workspace_check.
+ *   - A bounded device wait that gives up is reported through the residual:
+ *     the kernel writes NaN to d_residual instead of a sum (the error word
+ *     itself stays in the shared array and is cleared by the next call).
+ *     Callers who need the status code use jac_sweep_dev with their own
+ *     workspace and jac_workspace_check.
  * Errors: as jac_sweep_dev, plus JAC_EINVAL when the launch would need more
  * than JAC_NOALLOC_MAX_CTAS CTAs (a device with more SMs than that), and
  * JAC_ECUDA if the array's address cannot be obtained. */
@@ -215,18 +223,74 @@ jac_status jac_sweep_dev_noalloc(const jac_grid *g, const jac_plan *plan, int n_
                                  double *d_residual, void *stream);
 
 /* =====================================================================
- * Context API: one grid, resident in device memory owned by the context.
+ * Context API: one grid resident in device memory between the hoisted
+ * copy-in and copy-out (Sections 3.2-3.3: data transferred once, outside
+ * the outermost loop, and kept present on the device).  A context either
+ * owns its device memory (jac_create) or borrows all of it from the caller
+ * (jac_create_borrowed).
  * ===================================================================== */
 typedef struct jac_ctx jac_ctx;
 
-/* Create a context for an I x J x K grid.  Allocates the storage of all
- * fields, both state buffers, a FP64 staging array of I*J*K doubles and the
- * sweep workspace (cudaMalloc on the current device).  stream: the
- * cudaStream_t every call of this context uses (NULL: legacy default).
+/* Create a context for an I x J x K grid that owns its device memory: it
+ * allocates (cudaMalloc on the current device) the storage of all fields,
+ * both state buffers, a FP64 staging array of I*J*K doubles and the sweep
+ * workspace, and later the checkpoint tape (jac_tape_begin) and the
+ * asynchronous staging arrays (jac_upload_async).  stream: the cudaStream_t
+ * every call of this context uses (NULL: legacy default).
  * Errors: JAC_EINVAL (dims < 3, bad precision, omega not finite),
  * JAC_ENOMEM, JAC_ECUDA. */
 jac_status jac_create(jac_ctx **out, int I, int J, int K, jac_prec prec,
                       double omega, void *stream);
+
+/* What a borrowed context's workspace must hold besides the sweep scratch
+ * and one FP64 staging array: room for jac_upload_async's thirteen staging
+ * arrays (async_upload != 0), and a checkpoint tape of up to tape_max
+ * sweeps with a checkpoint every tape_C (tape_C = 0 or tape_max = 0: none);
+ * a later jac_tape_begin(C, max) fits if it needs no more state arrays
+ * (ceil(max / C) + C + 1) than that. */
+typedef struct jac_ws_spec {
+    int async_upload;
+    int tape_C;
+    int tape_max;
+} jac_ws_spec;
+
+/* Bytes of storage array `which` (JAC_P .. JAC_BND) of an I x J x K grid in
+ * precision prec: jac_pitch(I) * J * K elements of its element type.  Host
+ * only (no GPU needed).  Errors: JAC_EINVAL. */
+jac_status jac_field_bytes(int I, int J, int K, jac_prec prec, int which, size_t *bytes);
+
+/* Bytes of the workspace jac_create_borrowed needs for this grid and spec
+ * (NULL spec: no asynchronous staging, no tape): 256 + 8 *
+ * JAC_NOALLOC_MAX_CTAS bytes of sweep scratch, I*J*K doubles of staging,
+ * 13*I*J*K doubles with async_upload, and (ceil(max/C) + C + 1) state
+ * arrays plus 256 bytes for a tape; each part rounded up to 256 bytes.
+ * Host only (no GPU needed).  Errors: JAC_EINVAL. */
+jac_status jac_workspace_size(int I, int J, int K, jac_prec prec, const jac_ws_spec *spec,
+                              size_t *bytes);
+
+/* Create a context that allocates no device memory: the caller passes the
+ * grid's fourteen storage arrays in *fields (the jac_grid of the stateless
+ * API: dims, precision, omega, the two state buffers p[0], p[1] and
+ * coef[JAC_A0..JAC_BND], each of jac_field_bytes bytes, 16-byte aligned)
+ * and one workspace of at least jac_workspace_size(spec) bytes, 256-byte
+ * aligned.  All of it stays the caller's: it must outlive the context and
+ * is not freed by jac_destroy; the context only reads and writes it, on
+ * `stream`.  Upload, sweeps, residual, download, tape and adjoint work as
+ * for jac_create; the array contents are undefined until the first upload.
+ * jac_upload_async needs spec->async_upload, and jac_tape_begin a tape that
+ * fits spec; otherwise they return JAC_ENOMEM (jac_set_workspace gives the
+ * context a larger workspace).  Errors: JAC_EINVAL (bad grid, pointers,
+ * alignment or workspace size), JAC_ECUDA. */
+jac_status jac_create_borrowed(jac_ctx **out, const jac_grid *fields, void *stream,
+                               void *workspace, size_t ws_bytes, const jac_ws_spec *spec);
+
+/* Give a borrowed context another workspace (for example a larger one
+ * before a longer tape).  Synchronises the stream; the tape and the last
+ * residual are dropped (the field storage, and with it the state, is kept).
+ * The old workspace is no longer used once the call returns.  Errors:
+ * JAC_ESTATE for a context from jac_create, JAC_EINVAL as for
+ * jac_create_borrowed, JAC_ECUDA. */
+jac_status jac_set_workspace(jac_ctx *ctx, void *workspace, size_t ws_bytes, const jac_ws_spec *spec);
 
 /* Free everything the context owns (synchronises its stream).  NULL is ok. */
 jac_status jac_destroy(jac_ctx *ctx);
@@ -288,6 +352,20 @@ jac_status jac_download_async(jac_ctx *ctx, double *p_host, double *res_host);
  * JAC_ETIMEOUT if a bounded device wait of an earlier sweep gave up (the
  * word is cleared), JAC_ECUDA on a CUDA error. */
 jac_status jac_sync(jac_ctx *ctx);
+
+/* Failure-path test aid (host-side injection; the paper has no counterpart:
+ * its offload search gives up on a measurement after a time limit, Section
+ * 5.1.2, and this library's kernels likewise give up their device waits).
+ * The next sweep launch of this context is made with a grid-barrier target
+ * between sweeps that no CTA ever reaches, and with wait_ns nanoseconds as
+ * the limit of every wait on other warps and CTAs (wait_ns = 0 cancels;
+ * at most 2 s).  A launch of at least two sweeps then gives up its waits,
+ * every CTA drains its own copies and exits, the workspace error word is
+ * set and the residual of the launch is NaN: jac_residual, jac_sync and
+ * jac_download report JAC_ETIMEOUT and clear the word.  The state of that
+ * launch is partly swept; upload again before sweeping on.  Nothing faults
+ * or hangs: every wait is bounded.  Errors: JAC_EINVAL. */
+jac_status jac_inject_stall(jac_ctx *ctx, unsigned long long wait_ns);
 
 /* Sweeps completed since the last upload. */
 jac_status jac_sweep_count(const jac_ctx *ctx, long long *out);

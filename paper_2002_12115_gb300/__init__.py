@@ -13,8 +13,8 @@ include/jacobi.h, with hand-written sm_103a CUDA kernels.
         p = jac.download()        # one copy-out
 """
 from .binding import (FIELDS, KDEPTH_BALANCED, PRECS, JacError, Jacobi, JacobiBatch, adjoint_step_dev, check,
-                      jac_fields, jac_grid, jac_plan, lib, pack_dev, pitch, resolve_plan, stream_handle, sweep_dev,
-                      unpack_dev, workspace_check, workspace_size)
+                      ctx_workspace_size, field_bytes, jac_fields, jac_grid, jac_plan, jac_ws_spec, lib, pack_dev,
+                      pitch, resolve_plan, stream_handle, sweep_dev, unpack_dev, workspace_check, workspace_size)
 
 
 def __getattr__(name):
@@ -26,5 +26,6 @@ def __getattr__(name):
 
 
 __all__ = ["FIELDS", "KDEPTH_BALANCED", "PRECS", "JacError", "Jacobi", "JacobiBatch", "JacobiSweep",
-           "adjoint_step_dev", "check", "jac_fields", "jac_grid", "jac_plan", "jacobi_sweep", "lib", "pack_dev",
-           "pitch", "resolve_plan", "stream_handle", "sweep_dev", "unpack_dev", "workspace_check", "workspace_size"]
+           "adjoint_step_dev", "check", "ctx_workspace_size", "field_bytes", "jac_fields", "jac_grid", "jac_plan",
+           "jac_ws_spec", "jacobi_sweep", "lib", "pack_dev", "pitch", "resolve_plan", "stream_handle", "sweep_dev",
+           "unpack_dev", "workspace_check", "workspace_size"]

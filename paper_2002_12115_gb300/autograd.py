@@ -33,7 +33,9 @@ class JacobiSweep(torch.autograd.Function):
         cc = coefs.contiguous()
         for q, name in enumerate(COEF_ORDER):
             fields[name] = cc[q]
-        jac = Jacobi(I, J, K, prec, omega)
+        # a borrowed context: storage, staging and the tape are torch tensors
+        # (the caching allocator), sized for this tape up front
+        jac = Jacobi(I, J, K, prec, omega, tape=(C, T) if T > 0 else None)
         jac.upload_tensors(fields)
         if T > 0:
             jac.tape_begin(C, T)
@@ -47,6 +49,9 @@ class JacobiSweep(torch.autograd.Function):
     @staticmethod
     def backward(ctx, g):
         jac = ctx.jac
+        if jac is None:
+            raise RuntimeError("JacobiSweep supports one backward pass per forward: its tape is released "
+                               "after the first (retain_graph=True does not keep it)")
         need_p0, need_w, need_a3, need_c = ctx.needs_input_grad[:4]
         if ctx.T == 0:
             z = torch.zeros_like(g)

@@ -49,6 +49,10 @@ class jac_plan(ctypes.Structure):
                 ("fuse", ctypes.c_int)]
 
 
+class jac_ws_spec(ctypes.Structure):
+    _fields_ = [("async_upload", ctypes.c_int), ("tape_C", ctypes.c_int), ("tape_max", ctypes.c_int)]
+
+
 _VP = ctypes.c_void_p
 _I = ctypes.c_int
 _SIG = {
@@ -64,6 +68,12 @@ _SIG = {
     "jac_pack_dev": (_I, [_I, _I, _I, _I, _I, _VP, _VP, _VP]),
     "jac_unpack_dev": (_I, [_I, _I, _I, _I, _I, _VP, _VP, _VP]),
     "jac_create": (_I, [ctypes.POINTER(_VP), _I, _I, _I, _I, ctypes.c_double, _VP]),
+    "jac_field_bytes": (_I, [_I, _I, _I, _I, _I, ctypes.POINTER(ctypes.c_size_t)]),
+    "jac_workspace_size": (_I, [_I, _I, _I, _I, ctypes.POINTER(jac_ws_spec), ctypes.POINTER(ctypes.c_size_t)]),
+    "jac_create_borrowed": (_I, [ctypes.POINTER(_VP), ctypes.POINTER(jac_grid), _VP, _VP, ctypes.c_size_t,
+                                 ctypes.POINTER(jac_ws_spec)]),
+    "jac_set_workspace": (_I, [_VP, _VP, ctypes.c_size_t, ctypes.POINTER(jac_ws_spec)]),
+    "jac_inject_stall": (_I, [_VP, ctypes.c_ulonglong]),
     "jac_destroy": (_I, [_VP]),
     "jac_last_error": (ctypes.c_char_p, [_VP]),
     "jac_set_plan": (_I, [_VP, ctypes.POINTER(jac_plan)]),
@@ -143,32 +153,121 @@ def _host_ptr(a: np.ndarray) -> int:
     return a.ctypes.data
 
 
+def field_bytes(I: int, J: int, K: int, prec: str, which: int) -> int:
+    """Bytes of storage array `which` (index into FIELDS) of an I x J x K grid."""
+    n = ctypes.c_size_t()
+    check(lib().jac_field_bytes(int(I), int(J), int(K), PRECS[prec], int(which), ctypes.byref(n)))
+    return n.value
+
+
+def ctx_workspace_size(I: int, J: int, K: int, prec: str, async_upload: bool = False, tape=None) -> int:
+    """Bytes of the workspace a borrowed context needs (jac_workspace_size);
+    tape = (C, max_sweeps) reserves a checkpoint tape."""
+    C, mx = tape if tape else (0, 0)
+    n = ctypes.c_size_t()
+    check(lib().jac_workspace_size(int(I), int(J), int(K), PRECS[prec],
+                                   ctypes.byref(jac_ws_spec(int(bool(async_upload)), int(C), int(mx))),
+                                   ctypes.byref(n)))
+    return n.value
+
+
+def _tape_states(C: int, mx: int) -> int:
+    if C < 1 or mx < 1:
+        return 0
+    c = min(C, mx)
+    return (mx + c - 1) // c + c + 1
+
+
 class Jacobi:
     """One grid resident on the GPU (a jac_ctx).
 
     ``upload`` -> ``sweep(n)`` -> ``residual()`` / ``download()`` is the
     hoisted structure: one copy-in, n sweeps on resident arrays, one copy-out.
     Arrays are (K, J, I) float64, i fastest.
+
+    By default the context is borrowed (jac_create_borrowed): the fourteen
+    storage arrays and the workspace are torch tensors held by this object,
+    so every device byte comes from torch's allocator and the library
+    allocates none.  ``async_upload`` and ``tape=(C, max_sweeps)`` size the
+    workspace up front; later calls that need more (upload_async, a longer
+    tape) give the context a larger torch workspace.  ``owned=True`` makes
+    the library allocate instead (jac_create).
     """
 
-    def __init__(self, I: int, J: int, K: int, prec: str = "f32", omega: float = 0.8, stream=None):
+    def __init__(self, I: int, J: int, K: int, prec: str = "f32", omega: float = 0.8, stream=None,
+                 owned: bool = False, async_upload: bool = False, tape=None):
         import torch
         if prec not in PRECS:
             raise ValueError(f"prec must be one of {list(PRECS)}")
         self.I, self.J, self.K, self.prec, self.omega = int(I), int(J), int(K), prec, float(omega)
         self._stream_obj = stream if stream is not None else torch.cuda.current_stream()
         self.stream = stream_handle(self._stream_obj)
-        h = _VP()
-        check(lib().jac_create(ctypes.byref(h), self.I, self.J, self.K, PRECS[prec], self.omega,
-                               _VP(self.stream)))
-        self._h = h
+        self.owned = bool(owned)
         self._pending = []       # host arrays of asynchronous copies, until sync()
+        h = _VP()
+        if self.owned:
+            check(lib().jac_create(ctypes.byref(h), self.I, self.J, self.K, PRECS[prec], self.omega,
+                                   _VP(self.stream)))
+            self._h = h
+            return
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.storage = [torch.empty(field_bytes(self.I, self.J, self.K, prec, 0), dtype=torch.uint8, device=dev)
+                        for _ in range(2)]
+        self.storage += [torch.empty(field_bytes(self.I, self.J, self.K, prec, q), dtype=torch.uint8, device=dev)
+                         for q in range(1, NFIELDS)]
+        g = jac_grid()
+        g.I, g.J, g.K, g.prec, g.omega = self.I, self.J, self.K, PRECS[prec], self.omega
+        g.p[0], g.p[1] = self.storage[0].data_ptr(), self.storage[1].data_ptr()
+        for q in range(1, NFIELDS):
+            g.coef[q] = self.storage[q + 1].data_ptr()
+        self._spec = (bool(async_upload), tuple(tape) if tape else (0, 0))
+        spec = jac_ws_spec(int(self._spec[0]), *self._spec[1])
+        self.workspace = torch.empty(ctx_workspace_size(self.I, self.J, self.K, prec, *self._spec),
+                                     dtype=torch.uint8, device=dev)
+        check(lib().jac_create_borrowed(ctypes.byref(h), ctypes.byref(g), _VP(self.stream),
+                                        _VP(self.workspace.data_ptr()), ctypes.c_size_t(self.workspace.numel()),
+                                        ctypes.byref(spec)))
+        self._h = h
+
+    def device_bytes(self) -> int:
+        """Device bytes this object holds for a borrowed context (storage
+        arrays and workspace); 0 for an owned one."""
+        if self.owned:
+            return 0
+        return sum(t.numel() for t in self.storage) + self.workspace.numel()
+
+    def _ensure_workspace(self, async_upload: bool = False, tape=None) -> None:
+        """Borrowed contexts: a larger torch workspace if the current one
+        lacks the asynchronous staging or the tape asked for."""
+        if self.owned:
+            return
+        import torch
+        a0, t0 = self._spec
+        want_a = a0 or bool(async_upload)
+        want_t = t0
+        if tape is not None and _tape_states(*tape) > _tape_states(*t0):
+            want_t = tuple(tape)
+        if (want_a, want_t) == (a0, t0):
+            return
+        ws = torch.empty(ctx_workspace_size(self.I, self.J, self.K, self.prec, want_a, want_t),
+                         dtype=torch.uint8, device=self.workspace.device)
+        self._check(lib().jac_set_workspace(self._h, _VP(ws.data_ptr()), ctypes.c_size_t(ws.numel()),
+                                            ctypes.byref(jac_ws_spec(int(want_a), *want_t))))
+        self.workspace, self._spec = ws, (want_a, want_t)
+
+    def inject_stall(self, wait_ns: int) -> None:
+        """Failure-path test aid (jac_inject_stall): the next sweep launch
+        waits on a grid barrier nobody reaches, gives up after wait_ns and
+        reports JAC_ETIMEOUT."""
+        self._check(lib().jac_inject_stall(self._h, int(wait_ns)))
 
     # -- lifetime
     def close(self) -> None:
         if getattr(self, "_h", None):
             lib().jac_destroy(self._h)
             self._h = None
+        self.storage = []
+        self.workspace = None
 
     def __del__(self):
         try:
@@ -224,6 +323,7 @@ class Jacobi:
         """Copy in without waiting (pinned host arrays for an asynchronous
         copy).  The arrays are kept referenced until sync()."""
         f = self._fields(fields, device=False)
+        self._ensure_workspace(async_upload=True)
         self._check(lib().jac_upload_async(self._h, ctypes.byref(f)))
         self._pending.append(fields)
 
@@ -279,6 +379,7 @@ class Jacobi:
     # -- reverse mode
     def tape_begin(self, C: int, max_sweeps: int) -> None:
         """Record the next sweeps (at most max_sweeps) with a checkpoint every C."""
+        self._ensure_workspace(tape=(int(C), int(max_sweeps)))
         self._check(lib().jac_tape_begin(self._h, int(C), int(max_sweeps)))
 
     def tape_end(self) -> None:

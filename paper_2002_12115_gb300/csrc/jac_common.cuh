@@ -22,7 +22,10 @@ struct WsHeader {
 };
 constexpr size_t kWsHeaderBytes = 256;
 
-// Upper bound of a device-side wait before it gives up (nanoseconds).
+// Upper bound of a device-side wait before it gives up (nanoseconds).  A
+// launch may ask for a shorter bound on the waits that depend on the
+// progress of other warps or CTAs (SweepArgs::wait_ns); the waits that only
+// let a CTA's own copies land before it exits always keep this one.
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -73,14 +76,15 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 }
 
 // Wait for the phase with the given parity to complete; gives up after
-// kWaitLimitNs and returns false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+// limit_ns and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  unsigned long long limit_ns = kWaitLimitNs)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer_ns();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+        if (globaltimer_ns() - t0 > limit_ns) return false;
     }
 }
 
@@ -96,17 +100,22 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
 
-// Wait until *p >= target (acquire); false after kWaitLimitNs.
-__device__ __forceinline__ bool wait_counter_bounded(const unsigned *p, unsigned target)
+// Wait until *p >= target (acquire); false after limit_ns.
+__device__ __forceinline__ bool wait_counter_bounded(const unsigned *p, unsigned target,
+                                                     unsigned long long limit_ns = kWaitLimitNs)
 {
     if (ld_acquire_gpu(p) >= target) return true;
     const unsigned long long t0 = globaltimer_ns();
     while (true) {
         __nanosleep(64);
         if (ld_acquire_gpu(p) >= target) return true;
-        if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+        if (globaltimer_ns() - t0 > limit_ns) return false;
     }
 }
+
+// The workspace error word as it stands (an atomic read, so that the last
+// CTA of a launch sees every other CTA's abort).
+__device__ __forceinline__ bool workspace_failed(WsHeader *h) { return atomicOr(&h->errword, 0) != 0; }
 
 // 3-D tiled TMA load global -> shared, completion counted on `bar`.
 __device__ __forceinline__ void tma_load_3d(void *smem_dst, const CUtensorMap *map, uint64_t *bar, int x, int y,

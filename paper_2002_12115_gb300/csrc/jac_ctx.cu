@@ -1,9 +1,16 @@
-// Context API of libjac: one grid resident in device memory owned by the
-// context.  jac_upload is the hoisted copy-in, jac_sweep runs every sweep on
-// the resident arrays, jac_download is the hoisted copy-out -- the transfer
-// structure the paper builds its offloading on (Sections 3.2-3.3: transfer
-// nested-loop variables once, outside the outermost loop, batch the copies
-// and mark data already present on the device).
+// Context API of libjac: one grid resident in device memory.  jac_upload is
+// the hoisted copy-in, jac_sweep runs every sweep on the resident arrays,
+// jac_download is the hoisted copy-out -- the transfer structure the paper
+// builds its offloading on (Sections 3.2-3.3: transfer nested-loop variables
+// once, outside the outermost loop, batch the copies and mark data already
+// present on the device).
+//
+// Two ownership models.  jac_create allocates the field storage and every
+// scratch array itself (cudaMalloc).  jac_create_borrowed takes the fourteen
+// storage arrays and one workspace from the caller (for example torch
+// tensors) and allocates no device memory at all: staging, sweep scratch and
+// the checkpoint tape are carved out of the workspace, whose size
+// jac_workspace_size reports.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -32,6 +39,11 @@ struct jac_ctx {
     long long count = 0;
     bool uploaded = false;
     bool has_res = false;
+    unsigned long long stall_ns = 0;  // jac_inject_stall: the next sweep launch's wait limit
+    // borrowed contexts: caller memory, carved by ws_carve()
+    bool borrowed = false;
+    char *tape_region = nullptr;      // room for tape_cap state arrays plus 256 bytes
+    int tape_cap = 0;
     std::string err;
     // checkpoint tape of the sweeps since jac_tape_begin
     struct Tape {
@@ -85,6 +97,72 @@ jac_grid make_grid(const jac_ctx *c)
     return g;
 }
 
+// Sweep scratch of a borrowed context: the 256-byte header and one FP64
+// partial for each of up to JAC_NOALLOC_MAX_CTAS CTAs.  A sweep launches at
+// most one CTA per SM, so this covers every plan on any current GPU.
+constexpr size_t kBorrowedSweepScratch = jac::kWsHeaderBytes + (size_t)JAC_NOALLOC_MAX_CTAS * sizeof(double);
+
+// State arrays a tape of max_sweeps sweeps with a checkpoint every C holds:
+// its checkpoints, C - 1 segment states and two adjoint buffers.
+int tape_states(int C, int max_sweeps)
+{
+    if (C < 1 || max_sweeps < 1) return 0;
+    const int c = std::min(C, max_sweeps);
+    return (max_sweeps + c - 1) / c + c + 1;
+}
+
+// Layout of a borrowed context's workspace (every region 256-byte aligned).
+struct WsLayout {
+    size_t sweep = 0, staging = 0, stage_all = 0, tape = 0, total = 0;
+    int tape_states = 0;
+};
+
+WsLayout ws_layout(int I, int J, int K, jac_prec prec, const jac_ws_spec *spec)
+{
+    WsLayout L;
+    const size_t n = (size_t)I * J * K;
+    const size_t state = jac::round_up((size_t)jac_pitch(I) * J * K * jac::elem_bytes(prec, JAC_P), 256);
+    L.sweep = kBorrowedSweepScratch;
+    L.staging = jac::round_up(n * sizeof(double), 256);
+    L.stage_all = (spec && spec->async_upload) ? jac::round_up(JAC_NFIELDS * n * sizeof(double), 256) : 0;
+    L.tape_states = spec ? tape_states(spec->tape_C, spec->tape_max) : 0;
+    L.tape = L.tape_states ? (size_t)L.tape_states * state + 256 : 0;
+    L.total = L.sweep + L.staging + L.stage_all + L.tape;
+    return L;
+}
+
+jac_status check_spec(jac_ctx *c, const jac_ws_spec *spec)
+{
+    if (spec && (spec->tape_C < 0 || spec->tape_max < 0))
+        return ctx_fail(c, JAC_EINVAL, "negative tape size in the workspace spec");
+    return JAC_OK;
+}
+
+// Points the context at the regions of a borrowed workspace and clears its
+// sweep scratch (the kernels need a zero header).
+jac_status ws_carve(jac_ctx *c, void *ws, size_t ws_bytes, const jac_ws_spec *spec)
+{
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255))
+        return ctx_fail(c, JAC_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+    const WsLayout L = ws_layout(c->I, c->J, c->K, c->prec, spec);
+    if (ws_bytes < L.total)
+        return ctx_fail(c, JAC_EINVAL, "workspace too small: " + std::to_string(ws_bytes) + " bytes, need " +
+                                           std::to_string(L.total) + " (jac_workspace_size)");
+    char *p = static_cast<char *>(ws);
+    c->ws = p;
+    c->ws_bytes = L.sweep;
+    p += L.sweep;
+    c->staging = reinterpret_cast<double *>(p);
+    p += L.staging;
+    c->stage_all = L.stage_all ? reinterpret_cast<double *>(p) : nullptr;
+    p += L.stage_all;
+    c->tape_region = L.tape ? p : nullptr;
+    c->tape_cap = L.tape_states;
+    cudaError_t e = cudaMemsetAsync(c->ws, 0, L.sweep, c->stream);
+    if (e != cudaSuccess) return ctx_cuda(c, e, "cudaMemsetAsync");
+    return JAC_OK;
+}
+
 jac_status ensure_workspace(jac_ctx *c)
 {
     jac_grid g = make_grid(c);
@@ -92,6 +170,9 @@ jac_status ensure_workspace(jac_ctx *c)
     jac_status s = jac_sweep_workspace_size(&g, &c->plan, &need);
     if (s != JAC_OK) return ctx_from_thread(c, s);
     if (need <= c->ws_bytes) return JAC_OK;
+    if (c->borrowed)
+        return ctx_fail(c, JAC_EINVAL, "the sweep needs " + std::to_string(need) +
+                                           " bytes of scratch, more than a borrowed workspace holds");
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return ctx_cuda(c, e, "cudaStreamSynchronize");
     if (c->ws) cudaFree(c->ws);
@@ -109,7 +190,7 @@ void tape_free(jac_ctx *c)
 {
     if (c->tape.mem) {
         cudaStreamSynchronize(c->stream);
-        cudaFree(c->tape.mem);
+        if (!c->borrowed) cudaFree(c->tape.mem);
     }
     c->tape = jac_ctx::Tape();
 }
@@ -135,7 +216,13 @@ jac_status sweep_impl(jac_ctx *c, int n_iter)
             chunk = std::min(n_iter, tp.C - tp.taped % tp.C);
         }
         jac_grid g = make_grid(c);
-        s = jac::sweep_dev(&g, &c->plan, chunk, &hdr->residual, c->ws, c->ws_bytes, c->stream);
+        jac::LaunchOpts opts;
+        if (c->stall_ns) {            // the grid barrier of this launch is never reached
+            opts.wait_ns = c->stall_ns;
+            opts.gbar_extra = 1;
+            c->stall_ns = 0;
+        }
+        s = jac::sweep_dev(&g, &c->plan, chunk, &hdr->residual, c->ws, c->ws_bytes, c->stream, &opts);
         if (s != JAC_OK) return ctx_from_thread(c, s);
         c->cur = (c->cur + chunk) & 1;
         c->count += chunk;
@@ -159,6 +246,9 @@ jac_status upload_impl(jac_ctx *c, const jac_fields *f, Src from)
     for (int q = 0; q < JAC_NFIELDS; ++q)
         if (!f->f[q]) return ctx_fail(c, JAC_EINVAL, "field " + std::to_string(q) + " is NULL");
     const size_t n = (size_t)c->I * c->J * c->K;
+    if (from == Src::host_async && !c->stage_all && c->borrowed)
+        return ctx_fail(c, JAC_ENOMEM, "the borrowed workspace has no room for the asynchronous staging arrays "
+                                       "(jac_set_workspace with async_upload set)");
     if (from == Src::host_async && !c->stage_all) {
         cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&c->stage_all), JAC_NFIELDS * n * sizeof(double));
         if (e != cudaSuccess) {
@@ -264,12 +354,87 @@ jac_status jac_destroy(jac_ctx *c)
     if (!c) return JAC_OK;
     tape_free(c);
     cudaStreamSynchronize(c->stream);
+    if (c->borrowed) {                // nothing of the device memory is the context's
+        delete c;
+        return JAC_OK;
+    }
     if (c->ws) cudaFree(c->ws);
     if (c->staging) cudaFree(c->staging);
     if (c->stage_all) cudaFree(c->stage_all);
     if (c->arena) cudaFree(c->arena);
     delete c;
     return JAC_OK;
+}
+
+jac_status jac_field_bytes(int I, int J, int K, jac_prec prec, int which, size_t *bytes)
+{
+    if (!bytes) return ctx_fail(nullptr, JAC_EINVAL, "bytes is NULL");
+    if (I < 3 || J < 3 || K < 3) return ctx_fail(nullptr, JAC_EINVAL, "every grid dimension must be >= 3");
+    if (prec != JAC_F64 && prec != JAC_F32 && prec != JAC_F32_BF16COEF)
+        return ctx_fail(nullptr, JAC_EINVAL, "unknown precision");
+    if (which < 0 || which >= JAC_NFIELDS) return ctx_fail(nullptr, JAC_EINVAL, "bad array index");
+    *bytes = (size_t)jac_pitch(I) * J * K * jac::elem_bytes(prec, which);
+    return JAC_OK;
+}
+
+jac_status jac_workspace_size(int I, int J, int K, jac_prec prec, const jac_ws_spec *spec, size_t *bytes)
+{
+    if (!bytes) return ctx_fail(nullptr, JAC_EINVAL, "bytes is NULL");
+    if (I < 3 || J < 3 || K < 3) return ctx_fail(nullptr, JAC_EINVAL, "every grid dimension must be >= 3");
+    if (prec != JAC_F64 && prec != JAC_F32 && prec != JAC_F32_BF16COEF)
+        return ctx_fail(nullptr, JAC_EINVAL, "unknown precision");
+    jac_status s = check_spec(nullptr, spec);
+    if (s != JAC_OK) return s;
+    *bytes = ws_layout(I, J, K, prec, spec).total;
+    return JAC_OK;
+}
+
+jac_status jac_create_borrowed(jac_ctx **out, const jac_grid *fields, void *stream, void *workspace,
+                               size_t ws_bytes, const jac_ws_spec *spec)
+{
+    if (!out) return ctx_fail(nullptr, JAC_EINVAL, "out is NULL");
+    *out = nullptr;
+    jac_status s = jac::validate_grid(fields);
+    if (s != JAC_OK) return s;
+    if ((s = check_spec(nullptr, spec)) != JAC_OK) return s;
+    jac_ctx *c = new (std::nothrow) jac_ctx;
+    if (!c) return ctx_fail(nullptr, JAC_ENOMEM, "host allocation failed");
+    c->borrowed = true;
+    c->I = fields->I; c->J = fields->J; c->K = fields->K;
+    c->pitch = jac_pitch(c->I);
+    c->prec = fields->prec;
+    c->omega = fields->omega;
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->pbuf[0] = fields->p[0];
+    c->pbuf[1] = fields->p[1];
+    for (int q = JAC_A0; q <= JAC_BND; ++q) c->arr[q] = const_cast<void *>(fields->coef[q]);
+    if ((s = ws_carve(c, workspace, ws_bytes, spec)) != JAC_OK || (s = ensure_workspace(c)) != JAC_OK) {
+        delete c;
+        return s;
+    }
+    *out = c;
+    return JAC_OK;
+}
+
+jac_status jac_set_workspace(jac_ctx *c, void *workspace, size_t ws_bytes, const jac_ws_spec *spec)
+{
+    if (!c) return ctx_fail(c, JAC_EINVAL, "ctx is NULL");
+    if (!c->borrowed) return ctx_fail(c, JAC_ESTATE, "jac_set_workspace needs a context from jac_create_borrowed");
+    jac_status s = check_spec(c, spec);
+    if (s != JAC_OK) return s;
+    tape_free(c);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return ctx_cuda(c, e, "cudaStreamSynchronize");
+    c->has_res = false;                // the residual lived in the old workspace
+    if ((s = ws_carve(c, workspace, ws_bytes, spec)) != JAC_OK) {
+        c->ws = nullptr;               // no sweep until a workspace is set
+        c->ws_bytes = 0;
+        c->staging = c->stage_all = nullptr;
+        c->tape_region = nullptr;
+        c->tape_cap = 0;
+        return s;
+    }
+    return ensure_workspace(c);
 }
 
 const char *jac_last_error(const jac_ctx *c) { return c ? c->err.c_str() : jac::thread_last_error(); }
@@ -390,6 +555,16 @@ jac_status jac_tape_begin(jac_ctx *c, int C, int max_sweeps)
     tp.state_bytes = array_bytes(c, JAC_P);
     tp.n_ckpt = (max_sweeps + tp.C - 1) / tp.C;
     const size_t bytes = (size_t)(tp.n_ckpt + tp.C + 1) * tp.state_bytes + 256;
+    if (c->borrowed) {
+        const int need = tape_states(C, max_sweeps);
+        if (need > c->tape_cap)
+            return ctx_fail(c, JAC_ENOMEM, "this tape needs " + std::to_string(need) +
+                                               " state arrays; the borrowed workspace holds " +
+                                               std::to_string(c->tape_cap) + " (jac_set_workspace with a larger tape)");
+        tp.mem = c->tape_region;
+        c->tape = tp;
+        return JAC_OK;
+    }
     cudaError_t e = cudaMalloc(&tp.mem, bytes);
     if (e != cudaSuccess) return ctx_fail(c, JAC_ENOMEM, "tape allocation failed (" + std::to_string(bytes) + " bytes)");
     c->tape = tp;
@@ -453,6 +628,14 @@ jac_status jac_sweep_adjoint(jac_ctx *c, const double *lam_T, double *g_wrk1, do
         s = jac::unpack_dev(c->I, c->J, c->K, c->prec, JAC_P, tp.lam(lc), g_p0, c->stream);
         if (s != JAC_OK) return ctx_from_thread(c, s);
     }
+    return JAC_OK;
+}
+
+jac_status jac_inject_stall(jac_ctx *c, unsigned long long wait_ns)
+{
+    if (!c) return ctx_fail(c, JAC_EINVAL, "ctx is NULL");
+    if (wait_ns > jac::kWaitLimitNs) return ctx_fail(c, JAC_EINVAL, "wait_ns above the library's wait limit");
+    c->stall_ns = wait_ns;
     return JAC_OK;
 }
 

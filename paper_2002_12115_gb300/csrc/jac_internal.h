@@ -20,8 +20,16 @@ jac_status validate_grid(const jac_grid *g);
 jac_plan resolve_plan(const jac_grid *g, const jac_plan *plan);
 jac_plan resolve_plan_sms(const jac_grid *g, const jac_plan *plan, int sms);
 size_t sweep_workspace_bytes(const jac_grid *g, const jac_plan &p);
+// Launch options of the single-grid sweep that only a test of the failure
+// path sets: a shorter limit for the waits on other warps and CTAs, and an
+// offset that makes the grid barrier between sweeps unreachable.  Either one
+// set runs single sweeps (no two-sweep passes).
+struct LaunchOpts {
+    unsigned long long wait_ns = 0;
+    unsigned gbar_extra = 0;
+};
 jac_status sweep_dev(const jac_grid *g, const jac_plan *plan, int n_iter, double *d_residual, void *workspace,
-                     size_t ws_bytes, void *stream);
+                     size_t ws_bytes, void *stream, const LaunchOpts *opts = nullptr);
 jac_status pack_dev(int I, int J, int K, jac_prec prec, int which, const double *src, void *dst, cudaStream_t st);
 jac_status unpack_dev(int I, int J, int K, jac_prec prec, int which, const void *src, double *dst,
                       cudaStream_t st);

@@ -61,7 +61,27 @@ thread_local std::string g_err;
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_encode_once;
-int g_num_sms = 0;
+
+// Per-device attributes, cached by device ordinal (a process may drive
+// several GPUs of different kinds).
+constexpr int kMaxDevices = 64;
+std::mutex g_attr_mu;
+int g_num_sms[kMaxDevices] = {};
+size_t g_l2_bytes[kMaxDevices] = {};
+
+// Attribute `attr` of the current device, cached in table[dev]; `fallback`
+// when the device cannot be queried.
+template <typename V>
+V device_attr(V *table, cudaDeviceAttr attr, V fallback)
+{
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return fallback;
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    if (dev < kMaxDevices && table[dev] != 0) return table[dev];
+    if (cudaDeviceGetAttribute(&v, attr, dev) != cudaSuccess || v <= 0) return fallback;
+    if (dev < kMaxDevices) table[dev] = (V)v;
+    return (V)v;
+}
 
 jac_status fail(jac_status st, const std::string &msg)
 {
@@ -107,20 +127,8 @@ jac_status encode_map(CUtensorMap *m, const void *base, size_t elem, int pitch, 
     return JAC_OK;
 }
 
-int num_sms();
-
-int num_sms()
-{
-    if (g_num_sms == 0) {
-        int dev = 0, n = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
-            g_num_sms = n;
-        else
-            g_num_sms = 148;
-    }
-    return g_num_sms;
-}
+// SM count of the current device (148 if it cannot be queried).
+int num_sms() { return device_attr<int>(g_num_sms, cudaDevAttrMultiProcessorCount, 148); }
 
 }  // namespace
 
@@ -173,19 +181,7 @@ void set_l2_policy(SweepArgs &a, jac_prec prec, size_t points)
     }
 }
 
-size_t device_l2_bytes()
-{
-    static size_t l2 = 0;
-    if (l2 == 0) {
-        int dev = 0, v = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, dev) == cudaSuccess &&
-            v > 0)
-            l2 = (size_t)v;
-        else
-            l2 = 1;
-    }
-    return l2;
-}
+size_t device_l2_bytes() { return device_attr<size_t>(g_l2_bytes, cudaDevAttrL2CacheSize, 1); }
 
 int vector_points(jac_prec prec) { return prec == JAC_F64 ? 2 : 4; }
 
@@ -463,8 +459,9 @@ bool use_two_sweep_passes(const jac_grid *g, const jac_plan &p, int n_iter)
 }
 
 jac_status sweep_dev(const jac_grid *g, const jac_plan *plan, int n_iter, double *d_residual, void *workspace,
-                     size_t ws_bytes, void *stream)
+                     size_t ws_bytes, void *stream, const LaunchOpts *opts)
 {
+    const bool injected = opts && (opts->wait_ns != 0 || opts->gbar_extra != 0);
     jac_status s = validate_grid(g);
     if (s != JAC_OK) return s;
     if (n_iter < 0) return fail(JAC_EINVAL, "n_iter must be >= 0");
@@ -476,7 +473,7 @@ jac_status sweep_dev(const jac_grid *g, const jac_plan *plan, int n_iter, double
     if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 15)) return fail(JAC_EINVAL, "bad workspace");
     const size_t need = sweep_workspace_bytes(g, p);
     if (ws_bytes < need) return fail(JAC_EINVAL, "workspace too small: need " + std::to_string(need) + " bytes");
-    if (use_two_sweep_passes(g, p, n_iter)) {
+    if (!injected && use_two_sweep_passes(g, p, n_iter)) {
         // an even number of passes keeps the state of n sweeps in p[n % 2];
         // the remaining 0..3 sweeps run singly and give the residual if any
         const int n_pass = (n_iter / 2) & ~1;
@@ -501,6 +498,10 @@ jac_status sweep_dev(const jac_grid *g, const jac_plan *plan, int n_iter, double
     a.partials = reinterpret_cast<double *>(static_cast<char *>(workspace) + kWsHeaderBytes);
     a.res = d_residual ? d_residual : &hdr->residual;
     a.hdr = hdr;
+    if (injected) {
+        a.wait_ns = opts->wait_ns;
+        a.gbar_extra = opts->gbar_extra;
+    }
     const unsigned nblocks = (unsigned)std::min<long long>(sweep_units(g, p), num_sms());
     if (p.kdepth == JAC_KDEPTH_BALANCED) {
         // item numbers b + n G for n below the most tiles one CTA's range touches

@@ -449,6 +449,7 @@ k_sweep2(const __grid_constant__ Sweep2Desc d, const Sweep2Args a)
 
     // CTA epilogue: the last CTA to finish sums the partials in CTA order
     // and resets the workspace counters for the next launch.
+    // If any CTA gave up a wait, the residual is written as NaN.
     __syncthreads();
     __shared__ int s_last;
     if (threadIdx.x == 0) {
@@ -460,10 +461,14 @@ k_sweep2(const __grid_constant__ Sweep2Desc d, const Sweep2Args a)
     if (s_last) {
         __threadfence();
         if (threadIdx.x == 0) {
-            if (a.res != nullptr && !s_abort) {
-                double sum = 0.0, comp = 0.0;
-                for (int b = 0; b < G; ++b) neumaier_add(sum, comp, __ldcg(&a.partials[b]));
-                *a.res = sum + comp;
+            if (a.res != nullptr) {
+                if (s_abort || workspace_failed(a.hdr)) {
+                    *a.res = __longlong_as_double(0x7ff8000000000000ll);
+                } else {
+                    double sum = 0.0, comp = 0.0;
+                    for (int b = 0; b < G; ++b) neumaier_add(sum, comp, __ldcg(&a.partials[b]));
+                    *a.res = sum + comp;
+                }
             }
             a.hdr->gbar = 0u;
             a.hdr->counter = 0u;

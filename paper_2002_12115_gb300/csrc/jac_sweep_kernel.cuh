@@ -71,7 +71,16 @@ struct SweepArgs {
     int l2_keep_state;         // 1: state copies/stores evict_last, coefficients evict_first
     unsigned l2_keep_coef;     // bit q (JAC_A0..JAC_BND): array q's copies evict_last too
     long long bal_units;       // balanced ranges (BAL kernels): tile-planes of the grid
+    unsigned long long wait_ns;  // limit of the waits on other warps and CTAs (0: kWaitLimitNs)
+    unsigned gbar_extra;       // added to every grid-barrier target: 0, except when a test
+                               // makes the barrier unreachable so that its bounded wait runs out
 };
+
+// The limit of a launch's progress waits.
+__device__ __forceinline__ unsigned long long progress_limit(const SweepArgs &a)
+{
+    return a.wait_ns ? a.wait_ns : kWaitLimitNs;
+}
 
 // Fast2Sum step (Dekker): hi + b = s + err exactly when |hi| >= |b|.
 __device__ __forceinline__ void fast_two_sum_acc(float &hi, float &lo, float b)
@@ -332,6 +341,7 @@ k_sweep(const __grid_constant__ GridDesc d0, const SweepArgs a)
         if (lane == 0) {
             const uint64_t pol = l2_policy(a.l2_keep_state ? -1 : 0);
             const uint64_t pol_keep = l2_policy(1);
+            const unsigned long long wlim = progress_limit(a);
             uint32_t cc = 0;
             bool ok = true;
             for (int t = 0; t < n_iter && ok; ++t)
@@ -340,7 +350,7 @@ k_sweep(const __grid_constant__ GridDesc d0, const SweepArgs a)
                     if (BAL && it.nout == 0) continue;
                     for (int m = 0; m < it.nout; ++m, ++cc) {
                         const uint32_t slot = cc % RC, use = cc / RC;
-                        if (use > 0 && !mbar_wait_bounded(&c_empty[slot], (use - 1) & 1)) { ok = false; break; }
+                        if (use > 0 && !mbar_wait_bounded(&c_empty[slot], (use - 1) & 1, wlim)) { ok = false; break; }
                         if (s_abort) { ok = false; break; }
                         unsigned char *st = ring_c + (size_t)slot * S::C_STRIDE;
                         mbar_arrive_expect_tx(&c_full[slot], S::C_TX);
@@ -362,11 +372,15 @@ k_sweep(const __grid_constant__ GridDesc d0, const SweepArgs a)
         // -------------------------------------------------- state producer
         if (lane == 0) {
             const uint64_t pol = l2_policy(a.l2_keep_state ? 1 : 0);
+            const unsigned long long wlim = progress_limit(a);
             uint32_t pc = 0;
             bool ok = true;
             for (int t = 0; t < n_iter && ok; ++t) {
                 if (t > 0) {
-                    if (!wait_counter_bounded(&a.hdr->gbar, (unsigned)t * G)) { ok = false; break; }
+                    if (!wait_counter_bounded(&a.hdr->gbar, (unsigned)t * G + a.gbar_extra, wlim)) {
+                        ok = false;
+                        break;
+                    }
                     fence_proxy_async_global();
                 }
                 const int rb = (t + a.par) & 1;
@@ -377,7 +391,7 @@ k_sweep(const __grid_constant__ GridDesc d0, const SweepArgs a)
                     const uint32_t tx = it.D->p_tx;
                     for (int q = 0; q < it.nout + 2; ++q, ++pc) {
                         const uint32_t slot = pc % RP, use = pc / RP;
-                        if (use > 0 && !mbar_wait_bounded(&p_empty[slot], (use - 1) & 1)) { ok = false; break; }
+                        if (use > 0 && !mbar_wait_bounded(&p_empty[slot], (use - 1) & 1, wlim)) { ok = false; break; }
                         if (s_abort) { ok = false; break; }
                         mbar_arrive_expect_tx(&p_full[slot], tx);
                         tma_load_3d_hint(base + (size_t)slot * S::P_STRIDE, pm, &p_full[slot], it.i0 - H,
@@ -399,6 +413,7 @@ k_sweep(const __grid_constant__ GridDesc d0, const SweepArgs a)
         const int wy = warp;
         const T omega = (T)a.omega;
         const uint64_t st_pol = l2_policy(a.l2_keep_state ? 1 : 0);
+        const unsigned long long wlim = progress_limit(a);
         uint32_t pc = 0, cc = 0;
         bool ok = true;
         double acc = 0.0;
@@ -408,7 +423,7 @@ k_sweep(const __grid_constant__ GridDesc d0, const SweepArgs a)
         auto cons_sync = [&]() -> bool {
             __syncwarp();
             if (lane == 0) mbar_arrive(&cons_bar);
-            const bool r = mbar_wait_bounded(&cons_bar, sync_phase & 1);
+            const bool r = mbar_wait_bounded(&cons_bar, sync_phase & 1, wlim);
             ++sync_phase;
             return __all_sync(0xffffffffu, r);
         };
@@ -465,12 +480,12 @@ k_sweep(const __grid_constant__ GridDesc d0, const SweepArgs a)
 
                 for (int m = 0; m < it.nout; ++m, off += plane) {
                     if (m == 0) {
-                        ok = mbar_wait_bounded(&p_full[pc % RP], (pc / RP) & 1) &&
-                             mbar_wait_bounded(&p_full[(pc + 1) % RP], ((pc + 1) / RP) & 1);
+                        ok = mbar_wait_bounded(&p_full[pc % RP], (pc / RP) & 1, wlim) &&
+                             mbar_wait_bounded(&p_full[(pc + 1) % RP], ((pc + 1) / RP) & 1, wlim);
                     }
                     const uint32_t q2 = pc + m + 2;
-                    ok = ok && mbar_wait_bounded(&p_full[q2 % RP], (q2 / RP) & 1);
-                    ok = ok && mbar_wait_bounded(&c_full[cc % RC], (cc / RC) & 1);
+                    ok = ok && mbar_wait_bounded(&p_full[q2 % RP], (q2 / RP) & 1, wlim);
+                    ok = ok && mbar_wait_bounded(&c_full[cc % RC], (cc / RC) & 1, wlim);
                     ok = __all_sync(0xffffffffu, ok && !s_abort);
                     if (!ok) break;
 
@@ -582,9 +597,12 @@ k_sweep(const __grid_constant__ GridDesc d0, const SweepArgs a)
     }
 
     // CTA epilogue: the last CTA to finish sums each grid's partials in CTA
-    // order and resets the workspace counters for the next launch.
+    // order and resets the workspace counters for the next launch.  If any
+    // CTA gave up a wait (the error word is set), the partials may be stale
+    // and every residual is written as NaN instead, so that a caller who
+    // reads only the residual still sees the failure.
     __syncthreads();
-    __shared__ int s_last;
+    __shared__ int s_last, s_failed;
     if (threadIdx.x == 0) {
         __threadfence();
         const unsigned prev = atomicAdd(&a.hdr->counter, 1u);
@@ -593,11 +611,14 @@ k_sweep(const __grid_constant__ GridDesc d0, const SweepArgs a)
     __syncthreads();
     if (s_last) {
         __threadfence();
-        if (a.res != nullptr && !s_abort) {
+        if (threadIdx.x == 0) s_failed = s_abort || workspace_failed(a.hdr);
+        __syncthreads();
+        if (a.res != nullptr) {
             for (int g = threadIdx.x; g < a.ngrids; g += blockDim.x) {
                 double s = 0.0, c = 0.0;
-                for (int b = 0; b < G; ++b) neumaier_add(s, c, __ldcg(&a.partials[(size_t)g * G + b]));
-                a.res[g] = s + c;
+                if (!s_failed)
+                    for (int b = 0; b < G; ++b) neumaier_add(s, c, __ldcg(&a.partials[(size_t)g * G + b]));
+                a.res[g] = s_failed ? __longlong_as_double(0x7ff8000000000000ll) : s + c;
             }
         }
         __syncthreads();

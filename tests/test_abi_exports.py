@@ -74,3 +74,35 @@ def test_header_is_plain_c(tmp_path):
                         str(src), "-o", str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     assert subprocess.run([str(exe)]).returncode == 0
+
+
+def test_borrowed_sizes_without_gpu():
+    """jac_field_bytes and jac_workspace_size are host-only: the storage of
+    each array is pitch * J * K elements of its type, and a borrowed
+    context's workspace is the sweep scratch (256 + 8 * 2048 bytes), one
+    FP64 staging array, thirteen more with asynchronous staging, and
+    ceil(max/C) + C + 1 state arrays plus 256 bytes for a tape, each part
+    rounded up to 256 bytes."""
+    import paper_2002_12115_gb300 as pkg
+
+    def r256(n):
+        return (n + 255) // 256 * 256
+
+    I, J, K = 129, 33, 17
+    pitch = pkg.pitch(I)
+    assert pitch == 136
+    for prec, p_elem, c_elem in (("f64", 8, 8), ("f32", 4, 4), ("bf16", 4, 2)):
+        assert pkg.field_bytes(I, J, K, prec, 0) == pitch * J * K * p_elem
+        assert pkg.field_bytes(I, J, K, prec, 11) == pitch * J * K * p_elem          # wrk1
+        assert pkg.field_bytes(I, J, K, prec, 4) == pitch * J * K * c_elem           # a3
+        n = I * J * K
+        base = 256 + 8 * 2048 + r256(8 * n)
+        assert pkg.ctx_workspace_size(I, J, K, prec) == base
+        assert pkg.ctx_workspace_size(I, J, K, prec, async_upload=True) == base + r256(13 * 8 * n)
+        state = r256(pitch * J * K * p_elem)
+        assert pkg.ctx_workspace_size(I, J, K, prec, tape=(5, 20)) == base + (4 + 5 + 1) * state + 256
+        assert pkg.ctx_workspace_size(I, J, K, prec, tape=(10, 3)) == base + (1 + 3 + 1) * state + 256
+    with pytest.raises(pkg.JacError):
+        pkg.field_bytes(2, 5, 5, "f32", 0)
+    with pytest.raises(pkg.JacError):
+        pkg.field_bytes(5, 5, 5, "f32", 13)

@@ -21,8 +21,19 @@ def run_bench(*args, timeout=600):
     return json.loads(lines[0])
 
 
+def test_default_workload_is_the_largest_grid():
+    """With no flags the benchmark times the 513 x 513 x 1025 FP32 workload
+    (100 device-resident sweeps), on both arms."""
+    sys.path.insert(0, ROOT)
+    import bench
+    args = bench.parse_args([])
+    w = bench.WORKLOADS[args.workload]
+    assert (w["I"], w["J"], w["K"], w["sweeps"], w["prec"]) == (513, 513, 1025, 100, "f32")
+    assert args.steps >= 1 and args.warmup >= 3
+
+
 def test_reference_arm_line():
-    d = run_bench("--impl", "reference", "--steps", "1", "--warmup", "0")
+    d = run_bench("--impl", "reference", "--workload", "config2", "--steps", "1", "--warmup", "0")
     for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
                 "higher_is_better", "scaling", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert key in d, key

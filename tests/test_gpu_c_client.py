@@ -1,7 +1,9 @@
 """The C ABI from a plain C program: tests/c_client/jac_client.c, built with
 gcc against include/jacobi.h and linked to libjac.so, runs the hoisted path
-on the GPU.  Its state and residual equal, bitwise, the same calls made
-through the Python binding, and match the FP64 CPU oracle."""
+on the GPU, with a context that owns its memory and with a borrowed one
+whose storage and workspace the client allocates.  Its state and residual
+equal, bitwise, the same calls made through the Python binding, and match
+the FP64 CPU oracle."""
 import os
 import shutil
 import subprocess
@@ -32,23 +34,31 @@ def client(tmp_path_factory):
     d = tmp_path_factory.mktemp("c_client")
     exe = str(d / "jac_client")
     libdir = os.path.dirname(lib)
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    cuda = os.path.dirname(os.path.dirname(os.path.realpath(nvcc)))
+    cudalib = next((os.path.join(cuda, x) for x in ("lib64", "lib", "targets/sbsa-linux/lib",
+                                                     "targets/x86_64-linux/lib")
+                    if os.path.exists(os.path.join(cuda, x, "libcudart.so"))), os.path.join(cuda, "lib64"))
     r = subprocess.run([cc, "-std=c99", "-O2", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        "-I", os.path.join(cuda, "include"),
                         os.path.join(ROOT, "tests", "c_client", "jac_client.c"), "-o", exe,
-                        "-L", libdir, "-ljac", "-Wl,-rpath," + libdir], capture_output=True, text=True)
+                        "-L", libdir, "-ljac", "-Wl,-rpath," + libdir,
+                        "-L", cudalib, "-lcudart", "-Wl,-rpath," + cudalib], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     return exe, d
 
 
+@pytest.mark.parametrize("borrowed", [False, True])
 @pytest.mark.parametrize("prec,dims,n", [("f64", (33, 33, 65), 20), ("f32", (131, 10, 6), 5),
                                          ("bf16", (67, 19, 23), 7)])
-def test_c_client_matches_binding_and_oracle(client, prec, dims, n):
+def test_c_client_matches_binding_and_oracle(client, prec, dims, n, borrowed):
     exe, d = client
     I, J, K = dims
     f = ji.himeno_fields(I, J, K, seed=400 + I)
-    src, dst = d / f"in_{prec}.bin", d / f"out_{prec}.bin"
+    src, dst = d / f"in_{prec}.bin", d / f"out_{prec}_{int(borrowed)}.bin"
     np.concatenate([f[name].ravel() for name in ji.FIELD_NAMES]).astype(np.float64).tofile(src)
-    r = subprocess.run([exe, str(I), str(J), str(K), str(PRECS[prec]), str(n), str(src), str(dst)],
-                       capture_output=True, text=True)
+    r = subprocess.run([exe, str(I), str(J), str(K), str(PRECS[prec]), str(n), str(src), str(dst)]
+                       + (["borrowed"] if borrowed else []), capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     out = np.fromfile(dst, dtype=np.float64)
     p, g = out[:-1].reshape(K, J, I), float(out[-1])

@@ -4,9 +4,14 @@ jac_sweep_dev_noalloc serves callers that may not allocate device memory (a
 plugin handed only input and output buffers by a host that owns the GPU's
 memory, or a loop that cannot take cudaMalloc's synchronisation): it keeps
 its scratch in a fixed array inside the library instead of a caller
-workspace.  Two calls in a row must give what the workspace entry point
-gives, within the parity tolerance of each precision.  This file is
-collected last on purpose.
+workspace.  It launches the same kernel with the same plan as the
+workspace entry point, so two calls in a row must give that entry point's
+state and residual bit for bit, and both must match the oracle.
+
+The file name sorts last so that pytest collects it last: when a run stops
+at the first failure (-x), a failure here comes after every other test has
+run.  Nothing in it depends on the tests before it; it also passes alone in
+a fresh process.
 """
 import ctypes
 
@@ -14,7 +19,7 @@ import numpy as np
 import pytest
 
 import jacobi_inputs as ji
-from _util import TOL
+from _util import TOL, oracle_ref, rel_g, rel_p
 
 pytestmark = pytest.mark.gpu
 
@@ -101,17 +106,21 @@ def _no_alloc(pkg, grid, n, plan):
 
 @pytest.mark.parametrize("prec,dims,n,plan", [("f32", (130, 37, 41), 7, (8, 5)),
                                               ("bf16", (67, 29, 33), 4, (4, 3)),
-                                              ("f64", (70, 21, 19), 5, (8, 0))])
+                                              ("f64", (70, 21, 19), 5, (8, 0)),
+                                              # two-sweep passes (FP32, fuse = 2): 4 paired sweeps then 1 single
+                                              ("f32", (130, 37, 41), 9, (8, 5, 0, 2))])
 def test_no_alloc_matches_workspace_entry_point(L, prec, dims, n, plan):
     I, J, K = dims
-    grid = Grid(L, ji.himeno_fields(I, J, K, seed=200 + I), prec)
+    fields = ji.himeno_fields(I, J, K, seed=200 + I)
+    grid = Grid(L, fields, prec)
     want_p, want_g = _with_workspace(L, grid, n, plan)
     for call in range(2):                      # two calls in a row share the scratch
         grid.reset()
         p, g = _no_alloc(L, grid, n, plan)
-        err_p = np.abs(p - want_p).max() / np.abs(want_p).max()
-        err_g = abs(g - want_g) / abs(want_g)
-        assert err_p <= TOL[prec] and err_g <= TOL[prec], (call, err_p, err_g)
+        # the same kernel and plan: bit for bit
+        assert np.array_equal(p, want_p) and g == want_g, (call, rel_p(p, want_p), rel_g(g, want_g))
+    op, og = oracle_ref(fields, n, prec)
+    assert rel_p(p, op) <= TOL[prec] and rel_g(g, og) <= TOL[prec], (rel_p(p, op), rel_g(g, og))
 
 
 def test_no_alloc_scratch_covers_every_launch_of_this_gpu(L):
