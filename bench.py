@@ -58,6 +58,7 @@ WORKLOADS = {
     "large-bf16": dict(I=513, J=513, K=1025, sweeps=100, prec="bf16"),
     "large-f64": dict(I=513, J=513, K=1025, sweeps=100, prec="f64"),
     "medium": dict(I=257, J=257, K=513, sweeps=100, prec="f32"),
+    "profile": dict(I=257, J=257, K=257, sweeps=10, prec="f32"),
     "medium-bf16": dict(I=257, J=257, K=513, sweeps=100, prec="bf16"),
     "batch": dict(n_grids=512, sweeps=100, prec="f32"),
     "batch-f64": dict(n_grids=512, sweeps=100, prec="f64"),
