@@ -79,6 +79,14 @@ jac_status ctx_cuda(jac_ctx *c, cudaError_t e, const char *what)
     return ctx_fail(c, JAC_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// Bytes of data in storage array `which` (what a borrowed buffer holds).
+size_t data_bytes(const jac_ctx *c, int which)
+{
+    return (size_t)c->pitch * c->J * c->K * jac::elem_bytes(c->prec, which);
+}
+
+// The same rounded up to 256 bytes: the spacing of arrays inside the
+// context's own memory (arena, tape).
 size_t array_bytes(const jac_ctx *c, int which)
 {
     return jac::round_up((size_t)c->pitch * c->J * c->K * jac::elem_bytes(c->prec, which), 256);
@@ -209,7 +217,7 @@ jac_status sweep_impl(jac_ctx *c, int n_iter)
         int chunk = n_iter;
         if (tp.mem) {
             if (tp.taped % tp.C == 0) {
-                cudaError_t e = cudaMemcpyAsync(tp.ckpt(tp.taped / tp.C), c->pbuf[c->cur], tp.state_bytes,
+                cudaError_t e = cudaMemcpyAsync(tp.ckpt(tp.taped / tp.C), c->pbuf[c->cur], data_bytes(c, JAC_P),
                                                 cudaMemcpyDeviceToDevice, c->stream);
                 if (e != cudaSuccess) return ctx_cuda(c, e, "checkpoint copy");
             }
@@ -277,7 +285,7 @@ jac_status upload_impl(jac_ctx *c, const jac_fields *f, Src from)
                                      c->stream);
         if (s != JAC_OK) return ctx_from_thread(c, s);
     }
-    cudaError_t e = cudaMemcpyAsync(c->pbuf[1], c->pbuf[0], array_bytes(c, JAC_P), cudaMemcpyDeviceToDevice, c->stream);
+    cudaError_t e = cudaMemcpyAsync(c->pbuf[1], c->pbuf[0], data_bytes(c, JAC_P), cudaMemcpyDeviceToDevice, c->stream);
     if (e != cudaSuccess) return ctx_cuda(c, e, "device copy of p0");
     if (from == Src::host) {
         e = cudaStreamSynchronize(c->stream);
