@@ -47,6 +47,8 @@ TARGET_SEED = 43
 FD_SEED = 44
 #: seed of sampled check positions on large grids
 SAMPLE_SEED = 45
+#: seed of the complex fields of the 3-D FFT workload
+FFT_SEED = 46
 #: grid sizes the batched workload draws from
 BATCH_DIM_CHOICES = (17, 33, 49, 65, 97, 129)
 
@@ -250,3 +252,26 @@ def himeno_fields_torch(I: int, J: int, K: int, seed: int = SEED, device="cuda")
     bnd[1:K - 1, 1:J - 1, 1:I - 1] = 1.0
     f["bnd"] = bnd
     return {name: f[name] for name in FIELD_NAMES}
+
+
+# ------------------------------------------------------------------ FFT
+# Inputs of the 3-D FFT workload (the paper's second application, NAS.FT, is
+# an FFT code, Section 5.1.1).  A complex field of shape (n3, n2, n1), x
+# fastest: real parts are draws 1 .. N of the stream, imaginary parts draws
+# N+1 .. 2N, each U[-1, 1).
+def fft_field(n1: int, n2: int, n3: int, seed: int = FFT_SEED) -> np.ndarray:
+    """Seeded complex128 field of shape (n3, n2, n1)."""
+    N = n1 * n2 * n3
+    out = np.empty((n3, n2, n1), dtype=np.complex128)
+    out.real = uniform(seed, 0, N, -1.0, 1.0).reshape(n3, n2, n1)
+    out.imag = uniform(seed, N, N, -1.0, 1.0).reshape(n3, n2, n1)
+    return out
+
+
+def fft_field_torch(n1: int, n2: int, n3: int, seed: int = FFT_SEED, device="cuda"):
+    """fft_field as a complex128 torch tensor on ``device`` (bitwise equal)."""
+    import torch
+    N = n1 * n2 * n3
+    re = uniform_torch(seed, 0, N, -1.0, 1.0, device)
+    im = uniform_torch(seed, N, N, -1.0, 1.0, device)
+    return torch.complex(re, im).view(n3, n2, n1)
