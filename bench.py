@@ -59,6 +59,11 @@ WORKLOADS = {
     "large-f64": dict(I=513, J=513, K=1025, sweeps=100, prec="f64"),
     "medium": dict(I=257, J=257, K=513, sweeps=100, prec="f32"),
     "profile": dict(I=257, J=257, K=257, sweeps=10, prec="f32"),
+    # 3-D FFT block: the spectral step (inverse transform of U times the
+    # heat-equation decay, energy sum) on a 512^3 complex grid
+    "fft": dict(n=(512, 512, 512), prec="c32", alpha=1e-5),
+    "fft-c64": dict(n=(512, 512, 512), prec="c64", alpha=1e-5),
+    "fft-profile": dict(n=(256, 256, 256), prec="c32", alpha=1e-5),
     "medium-bf16": dict(I=257, J=257, K=513, sweeps=100, prec="bf16"),
     "batch": dict(n_grids=512, sweeps=100, prec="f32"),
     "batch-f64": dict(n_grids=512, sweeps=100, prec="f64"),
@@ -710,6 +715,106 @@ def bench_adjoint(args, w, stream, steps=3):
     return out
 
 
+FFT_BYTES_PER_POINT = {"c32": 3 * 2 * 8, "c64": 3 * 2 * 16}   # three passes, each reads and writes every point
+
+
+def bench_fft(args, w, stream, steps=None, warmup=None, e2e=True, parity=True):
+    """The spectral step of the 3-D FFT block: every step computes
+    inverse(U * exp(-4 pi^2 alpha t |kbar|^2)) and its energy for the next
+    time t (three passes, one launch each), U the forward transform of the
+    initial field computed once outside the loop.  Gpoint/s = grid points per
+    step / time.  e2e: the same step from pinned host memory (copy-in of the
+    initial field, forward transform, one spectral step, copy-out of u and of
+    the energy) through the C ABI."""
+    import numpy as np
+    import torch
+
+    import jacobi_inputs as ji
+    from paper_2002_12115_gb300 import FFT3
+    n1, n2, n3 = w["n"]
+    prec, alpha = w["prec"], w["alpha"]
+    steps = steps or args.steps
+    warmup = warmup or args.warmup
+    N = n1 * n2 * n3
+    cdt = torch.complex64 if prec == "c32" else torch.complex128
+    u0 = ji.fft_field_torch(n1, n2, n3).to(cdt)
+    out = {}
+    with FFT3(n1, n2, n3, prec, stream) as f:
+        U = f.forward(u0)
+        u = torch.empty_like(U)
+        energy = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for k in range(warmup):
+            f.evolve(U, alpha, 0.1 * (k + 1), out=u, energy=energy)
+        torch.cuda.synchronize()
+        a, b = events()
+        a.record(stream)
+        for k in range(steps):
+            f.evolve(U, alpha, 0.1 * (k + 1), out=u, energy=energy)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        gpts = N / (ms * 1e-3) / 1e9
+        peak, kind = measured_peak()
+        achieved = FFT_BYTES_PER_POINT[prec] * N / (ms * 1e-3) / 1e9
+        out.update({"value": gpts, "unit": "Gpoint/s (3-D FFT spectral steps)", "ms_per_step": ms,
+                    "grid": [n1, n2, n3], "prec": prec, "energy": float(energy.item()),
+                    "gflops_5nlogn": 5 * N * np.log2(N) / (ms * 1e-3) / 1e9,
+                    "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                 "frac": achieved / peak, "peak_kind": kind,
+                                 "bytes_per_point": FFT_BYTES_PER_POINT[prec],
+                                 "kernel": "k_fft_pass (3 launches per step)"}})
+        if e2e:
+            host_u0 = torch.empty(u0.shape, dtype=cdt, pin_memory=True)
+            host_u0.copy_(u0)
+            host_u = torch.empty(u0.shape, dtype=cdt, pin_memory=True)
+            host_e = torch.empty(1, dtype=torch.float64, pin_memory=True)
+            dev_u0 = torch.empty_like(u0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for k in range(steps):
+                dev_u0.copy_(host_u0, non_blocking=True)
+                f.forward(dev_u0, out=U)
+                f.evolve(U, alpha, 0.1 * (k + 1), out=u, energy=energy)
+                host_u.copy_(u, non_blocking=True)
+                host_e.copy_(energy, non_blocking=True)
+                torch.cuda.current_stream().synchronize()
+            e2e_ms = (time.perf_counter() - t0) * 1e3 / steps
+            out["e2e"] = {"value": N / (e2e_ms * 1e-3) / 1e9, "unit": "Gpoint/s (3-D FFT spectral steps)",
+                          "h2d_bytes_per_step": N * u0.element_size(), "d2h_bytes_per_step": N * u0.element_size() + 8,
+                          "how": "copy-in of the initial field, forward transform, one spectral step, copy-out of "
+                                 "the field and the energy, every step"}
+        if parity:
+            import oracle.fft as fo
+            fo.build()
+            u0h = u0.cpu().numpy().astype(np.complex128)
+            Uh = U.cpu().numpy().astype(np.complex128)
+            t_last = 0.1 * steps
+            f.evolve(U, alpha, t_last, out=u, energy=energy)
+            uh = u.cpu().numpy().astype(np.complex128)
+            pts = ji.interior_points(n1 + 2, n2 + 2, n3 + 2, 4, ji.SAMPLE_SEED) - 1     # 4 seeded indices
+            errs_U, errs_u = [], []
+            kz, ky, kx = (np.fft.fftfreq(n, 1.0 / n) for n in (n3, n2, n1))
+            c = -4.0 * np.pi ** 2 * alpha * t_last
+            fac = np.exp(c * (kz[:, None, None] ** 2 + ky[None, :, None] ** 2 + kx[None, None, :] ** 2))
+            W = Uh * fac
+            del fac
+            for (i, j, k) in pts:
+                errs_U.append(abs(fo.point(u0h, (i, j, k)) - Uh[k, j, i]))
+                errs_u.append(abs(fo.point(W, (i, j, k), sign=1) / N - uh[k, j, i]))
+            e_want = float(np.sum(np.abs(W) ** 2) / N)          # Parseval
+            out["parity"] = {"forward_err": max(errs_U) / float(np.abs(Uh).max()),
+                             "step_err": max(errs_u) / float(np.abs(uh).max()),
+                             "energy_err": abs(float(energy.item()) - e_want) / e_want,
+                             "tol": 1e-5 if prec == "c32" else 1e-12,
+                             "sample": "4 seeded output points of the forward transform and of the last step, each "
+                                       "the FP64 oracle's single-sum DFT over all points; the energy against "
+                                       "Parseval's sum |W|^2 / N of the step's spectrum"}
+            del u0h, Uh, uh, W
+    del u0
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_native(args, w, wname):
     import torch
 
@@ -757,6 +862,20 @@ def run_native(args, w, wname):
                      "config": {"workload": "512 grids, dims drawn from {17,33,49,65,97,129}, f32, 100 sweeps; "
                                             "plans searched from scratch"},
                      "searches": r})
+    if wname.startswith("fft"):
+        r = bench_fft(args, w, stream, parity=not args.no_parity, e2e=not args.no_e2e)
+        ms = max_over_ranks(r["ms_per_step"], args.dist)
+        n1, n2, n3 = w["n"]
+        return emit({"metric": "3-D FFT spectral step Gpoint/s & % HBM roofline", "value": r["value"] * world,
+                     "unit": r["unit"], "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                     "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                     "dtype": w["prec"], "data": "synthetic",
+                     "config": {"workload": f"{n1}x{n2}x{n3} {w['prec']} 3-D FFT spectral steps (heat equation, "
+                                            f"alpha {w['alpha']})",
+                                "l2": f"inputs larger than L2 ({n1 * n2 * n3 * (8 if w['prec'] == 'c32' else 16) / 1e6:.0f}"
+                                      " MB per array); no flush"},
+                     "roofline": dict(r["roofline"], traffic=None), "e2e": r.get("e2e"), "parity": r.get("parity"),
+                     "gpu_launches": 3 * args.steps, "fft": r})
     if wname.startswith("adjoint"):
         r = bench_adjoint(args, w, stream, steps=args.steps)
         ms = max_over_ranks(r["ms_per_pass"], args.dist)
@@ -808,6 +927,9 @@ def run_native(args, w, wname):
                 compare["config2_" + vp] = bench_variant(c2, vp, dev2, stream, 200 if vp == "f64" else 1000)
             del dev2
         compare["per_sweep_transfers"] = bench_unhoisted_grid(c2)
+        for key in ("fft", "fft-c64"):
+            compare[key.replace("-", "_")] = bench_fft(args, WORKLOADS[key], stream, steps=5, warmup=3, e2e=False,
+                                                        parity=False)
         compare["batched"] = bench_batch(args, stream, steps=2, autotune=not args.no_autotune)
         torch.cuda.empty_cache()
 

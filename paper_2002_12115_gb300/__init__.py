@@ -12,8 +12,8 @@ include/jacobi.h, with hand-written sm_103a CUDA kernels.
         gosa = jac.residual()     # residual of the last sweep
         p = jac.download()        # one copy-out
 """
-from .binding import (FIELDS, KDEPTH_BALANCED, PRECS, JacError, Jacobi, JacobiBatch, adjoint_step_dev, check,
-                      ctx_workspace_size, field_bytes, jac_fields, jac_grid, jac_plan, jac_ws_spec, lib, pack_dev,
+from .binding import (FFT3, FIELDS, KDEPTH_BALANCED, PRECS, JacError, Jacobi, JacobiBatch, adjoint_step_dev, check,
+                      ctx_workspace_size, fft_workspace_size, field_bytes, jac_fields, jac_grid, jac_plan, jac_ws_spec, lib, pack_dev,
                       pitch, resolve_plan, stream_handle, sweep_dev, unpack_dev, workspace_check, workspace_size)
 
 
@@ -25,7 +25,7 @@ def __getattr__(name):
     raise AttributeError(name)
 
 
-__all__ = ["FIELDS", "KDEPTH_BALANCED", "PRECS", "JacError", "Jacobi", "JacobiBatch", "JacobiSweep",
-           "adjoint_step_dev", "check", "ctx_workspace_size", "field_bytes", "jac_fields", "jac_grid", "jac_plan",
+__all__ = ["FFT3", "FIELDS", "KDEPTH_BALANCED", "PRECS", "JacError", "Jacobi", "JacobiBatch", "JacobiSweep",
+           "adjoint_step_dev", "check", "ctx_workspace_size", "fft_workspace_size", "field_bytes", "jac_fields", "jac_grid", "jac_plan",
            "jac_ws_spec", "jacobi_sweep", "lib", "pack_dev", "pitch", "resolve_plan", "stream_handle", "sweep_dev",
            "unpack_dev", "workspace_check", "workspace_size"]

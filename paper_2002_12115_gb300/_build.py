@@ -37,7 +37,7 @@ def sources() -> list[str]:
 def _deps() -> list[str]:
     deps = sources()
     deps += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
-    deps.append(os.path.join(INCLUDE, "jacobi.h"))
+    deps += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     return deps
 
 

@@ -107,6 +107,14 @@ _SIG = {
     "jac_batch_download_dev": (_I, [_VP, _I, _VP]),
     "jac_batch_info": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                             ctypes.POINTER(ctypes.c_longlong)]),
+    # 3-D FFT block (include/jfft.h)
+    "jfft_workspace_size": (_I, [_I, _I, _I, _I, ctypes.POINTER(ctypes.c_size_t)]),
+    "jfft_plan_create": (_I, [ctypes.POINTER(_VP), _I, _I, _I, _I, _VP, _VP, ctypes.c_size_t]),
+    "jfft_destroy": (_I, [_VP]),
+    "jfft_last_error": (ctypes.c_char_p, [_VP]),
+    "jfft_forward": (_I, [_VP, _VP, _VP]),
+    "jfft_inverse": (_I, [_VP, _VP, _VP]),
+    "jfft_evolve": (_I, [_VP, _VP, ctypes.c_double, ctypes.c_double, _VP, _VP]),
 }
 
 _lock = threading.Lock()
@@ -573,3 +581,95 @@ class JacobiBatch:
         self._check(lib().jac_batch_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
                                          ctypes.byref(d)))
         return {"items": a.value, "ctas": b.value, "warps": c.value, "sweeps": d.value}
+
+
+# ---------------------------------------------------------------- 3-D FFT
+FFT_PRECS = {"c64": 0, "c32": 1}
+
+
+def fft_workspace_size(n1: int, n2: int, n3: int, prec: str = "c32") -> int:
+    """Bytes of the workspace an FFT plan of this shape needs (jfft_workspace_size)."""
+    n = ctypes.c_size_t()
+    check(lib().jfft_workspace_size(int(n1), int(n2), int(n3), FFT_PRECS[prec], ctypes.byref(n)))
+    return n.value
+
+
+class FFT3:
+    """3-D complex FFT of an (n3, n2, n1) array (x fastest) on the GPU (a
+    jfft_plan).  The workspace is a torch tensor held by this object; data
+    arrays are complex64 ("c32") or complex128 ("c64") CUDA tensors."""
+
+    def __init__(self, n1: int, n2: int, n3: int, prec: str = "c32", stream=None):
+        import torch
+        if prec not in FFT_PRECS:
+            raise ValueError(f"prec must be one of {list(FFT_PRECS)}")
+        self.n1, self.n2, self.n3, self.prec = int(n1), int(n2), int(n3), prec
+        self.dtype = torch.complex64 if prec == "c32" else torch.complex128
+        self._stream_obj = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = stream_handle(self._stream_obj)
+        self.workspace = torch.empty(fft_workspace_size(n1, n2, n3, prec), dtype=torch.uint8, device="cuda")
+        h = _VP()
+        check(lib().jfft_plan_create(ctypes.byref(h), self.n1, self.n2, self.n3, FFT_PRECS[prec],
+                                     _VP(self.stream), _VP(self.workspace.data_ptr()),
+                                     ctypes.c_size_t(self.workspace.numel())))
+        self._h = h
+
+    @property
+    def shape(self):
+        return (self.n3, self.n2, self.n1)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().jfft_destroy(self._h)
+            self._h = None
+        self.workspace = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, st: int) -> None:
+        if st != JAC_OK:
+            msg = lib().jfft_last_error(self._h)
+            raise JacError(st, msg.decode() if msg else "")
+
+    def _arg(self, x, name):
+        if tuple(x.shape) != self.shape or x.dtype != self.dtype or not x.is_cuda or not x.is_contiguous():
+            raise ValueError(f"{name}: expected a contiguous {self.dtype} CUDA tensor of shape {self.shape}")
+        return _VP(x.data_ptr())
+
+    def forward(self, x, out=None):
+        """Unscaled forward transform; out may be x (in place)."""
+        import torch
+        out = torch.empty_like(x) if out is None else out
+        self._check(lib().jfft_forward(self._h, self._arg(x, "x"), self._arg(out, "out")))
+        return out
+
+    def inverse(self, X, out=None):
+        """Inverse transform scaled by 1/N; out may be X (in place)."""
+        import torch
+        out = torch.empty_like(X) if out is None else out
+        self._check(lib().jfft_inverse(self._h, self._arg(X, "X"), self._arg(out, "out")))
+        return out
+
+    def evolve(self, U, alpha: float, t: float, out=None, energy=None):
+        """The spectral step inverse(U * exp(-4 pi^2 alpha t |kbar|^2)); energy:
+        a float64 CUDA tensor of one element that receives sum |u|^2, or None."""
+        import torch
+        out = torch.empty_like(U) if out is None else out
+        ep = None
+        if energy is not None:
+            if energy.dtype != torch.float64 or not energy.is_cuda or energy.numel() < 1:
+                raise ValueError("energy: expected a float64 CUDA tensor")
+            ep = _VP(energy.data_ptr())
+        self._check(lib().jfft_evolve(self._h, self._arg(U, "U"), float(alpha), float(t), self._arg(out, "out"),
+                                      ep))
+        return out

@@ -7,12 +7,17 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "jacobi.h")
+HEADERS = sorted(os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+                 if f.endswith(".h"))
 
 
-def declared_functions(path=HEADER):
-    text = open(path).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(jac_[a-z0-9_]+)\s*\(", text)))
+def declared_functions(paths=HEADERS):
+    names = set()
+    for path in paths:
+        text = open(path).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names.update(re.findall(r"\b((?:jac|jfft)_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -24,9 +29,11 @@ def libjac():
 
 def test_header_declares_the_boundary():
     names = declared_functions()
-    for must in ("jac_create", "jac_upload", "jac_sweep", "jac_residual", "jac_download", "jac_destroy",
-                 "jac_sweep_dev", "jac_last_error"):
-        assert must in names
+    for must in ("jac_create", "jac_create_borrowed", "jac_workspace_size", "jac_upload", "jac_sweep",
+                 "jac_residual", "jac_download", "jac_destroy", "jac_sweep_dev", "jac_last_error",
+                 "jac_sweep_adjoint", "jac_batch_sweep", "jfft_plan_create", "jfft_forward", "jfft_inverse",
+                 "jfft_evolve"):
+        assert must in names, must
 
 
 def test_every_declared_symbol_is_exported(libjac):
@@ -66,7 +73,7 @@ def test_header_is_plain_c(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     src = tmp_path / "use_header.c"
-    src.write_text('#include "jacobi.h"\n'
+    src.write_text('#include "jacobi.h"\n#include "jfft.h"\n'
                    "int main(void) { jac_plan p = {8, JAC_KDEPTH_BALANCED, 0, 0};\n"
                    "  jac_fields f; (void)f; return p.kdepth == -1 && JAC_NOALLOC_MAX_CTAS == 2048 ? 0 : 1; }\n")
     exe = tmp_path / "use_header"
@@ -106,3 +113,14 @@ def test_borrowed_sizes_without_gpu():
         pkg.field_bytes(2, 5, 5, "f32", 0)
     with pytest.raises(pkg.JacError):
         pkg.field_bytes(5, 5, 5, "f32", 13)
+
+
+def test_fft_sizes_without_gpu():
+    """jfft_workspace_size is host-only and rejects extents that are not
+    powers of two in [2, 1024]."""
+    import paper_2002_12115_gb300 as pkg
+    assert pkg.fft_workspace_size(256, 256, 256, "c32") > 256 + 3 * 256 * 8
+    assert pkg.fft_workspace_size(64, 32, 16, "c64") >= 256 + (64 + 32 + 16) * 16
+    for bad in ((12, 16, 16), (1, 16, 16), (2048, 16, 16)):
+        with pytest.raises(pkg.JacError):
+            pkg.fft_workspace_size(*bad)
