@@ -661,6 +661,7 @@ def bench_tuners(stream, sweeps=100):
     out = {"default": {"value": rate(), "plans_measured": 0}}
     runs = (("cd_1pass", lambda: at.tune_batch(b, n_sweeps=10, reps=2, passes=1, cache_path=None)),
             ("cd_2pass", lambda: at.tune_batch(b, n_sweeps=10, reps=2, passes=2, cache_path=None)),
+            ("class_exhaustive", lambda: at.class_exhaustive_tune_batch(b, n_sweeps=10, reps=2)),
             ("ga_seed0", lambda: at.ga_tune_batch(b, M=10, T=10, n_sweeps=10, reps=2, seed=0)),
             ("ga_seed1", lambda: at.ga_tune_batch(b, M=10, T=10, n_sweeps=10, reps=2, seed=1)))
     for name, search in runs:
@@ -670,6 +671,41 @@ def bench_tuners(stream, sweeps=100):
         out[name] = {"value": rate(), "plans_measured": count["n"], "search_s": time.perf_counter() - t0,
                      "plan": {k: plan[k] for k in ("warps", "tile_i", "kdepth")}}
     b.close()
+    torch.cuda.empty_cache()
+
+    # a sub-batch small enough to search exhaustively: the grids of the
+    # batch with I in {33, 129} and K in {65, 129}, every plan of the space
+    sub_ids = [g for g, d in enumerate(dims) if d[0] in (33, 129) and d[2] in (65, 129)]
+    sub = [dims[g] for g in sub_ids]
+    nsub = sum((I - 2) * (J - 2) * (K - 2) for I, J, K in sub)
+    sb = JacobiBatch(sub, "f32", 0.8, stream)
+    for q, g in enumerate(sub_ids):
+        I, J, K = dims[g]
+        sb.upload_tensors(q, ji.himeno_fields_torch(I, J, K, seed=42 + g))
+    res = {"grids": len(sub)}
+
+    def sub_rate():
+        sb.sweep(sweeps, residuals=False)
+        return nsub * sweeps / at.time_call(lambda: sb.sweep(sweeps, residuals=False), 3, stream) / 1e9
+
+    sb.set_plan(0, None, None)
+    res["default"] = {"value": sub_rate()}
+    subruns = (("joint_exhaustive", lambda: at.joint_exhaustive_tune_batch(sb, n_sweeps=10, reps=2, warps=(8,))),
+               ("cd_1pass", lambda: at.tune_batch(sb, n_sweeps=10, reps=2, passes=1, warps=(8,), cache_path=None)),
+               ("class_exhaustive", lambda: at.class_exhaustive_tune_batch(sb, n_sweeps=10, reps=2, warps=(8,))),
+               ("ga_seed0", lambda: at.ga_tune_batch(sb, M=10, T=10, n_sweeps=10, reps=2, seed=0, warps=(8,))),
+               ("ga_seed1", lambda: at.ga_tune_batch(sb, M=10, T=10, n_sweeps=10, reps=2, seed=1, warps=(8,))))
+    for name, search in subruns:
+        t0 = time.perf_counter()
+        plan = search()
+        res[name] = {"value": sub_rate(), "search_s": time.perf_counter() - t0,
+                     "plan": {k: plan[k] for k in ("warps", "tile_i", "kdepth")}}
+        if name == "joint_exhaustive":
+            ts = plan["times"]
+            res[name].update({"plans_measured": plan["measured"], "best_ms_per_sweep": ts[0] * 1e3,
+                              "median_ms_per_sweep": ts[len(ts) // 2] * 1e3, "worst_ms_per_sweep": ts[-1] * 1e3})
+    sb.close()
+    out["sub_batch_exhaustive"] = res
     torch.cuda.empty_cache()
     return out
 

@@ -148,6 +148,66 @@ def himeno_fields(I: int, J: int, K: int, seed: int = SEED) -> dict[str, np.ndar
     return {name: f[name] for name in FIELD_NAMES}
 
 
+def himeno_fields_box(I: int, J: int, K: int, lo, hi, seed: int = SEED) -> dict[str, np.ndarray]:
+    """The arrays of himeno_fields(I, J, K) restricted to the box
+    lo <= (i, j, k) < hi, drawn directly: the generator is counter based, so
+    each row of the box is the stretch of draws at its flat indices.  Equal,
+    bitwise, to slicing the full arrays (tested); for sampled checks of grids
+    too large to generate whole on the host."""
+    (i0, j0, k0), (i1, j1, k1) = lo, hi
+    if not (0 <= i0 < i1 <= I and 0 <= j0 < j1 <= J and 0 <= k0 < k1 <= K):
+        raise ValueError("box outside the grid")
+    N = I * J * K
+    ni, nj, nk = i1 - i0, j1 - j0, k1 - k0
+    flat = ((np.arange(k0, k1, dtype=np.uint64)[:, None, None] * np.uint64(J)
+             + np.arange(j0, j1, dtype=np.uint64)[None, :, None]) * np.uint64(I)
+            + np.arange(i0, i1, dtype=np.uint64)[None, None, :])
+    f: dict[str, np.ndarray] = {}
+    with np.errstate(over="ignore"):
+        for q, name in enumerate(DRAW_ORDER):
+            lo_v, hi_v = _RANGES[name]
+            n = flat + np.uint64(q * N + 1)          # 1-based draw numbers of the box's points
+            z = np.uint64(seed & _MASK64) + n * GAMMA
+            f[name] = lo_v + (hi_v - lo_v) * _unit(_mix(z))
+    s = f["a0"] + f["a1"]
+    s += f["a2"]
+    s += f["c0"]
+    s += f["c1"]
+    s += f["c2"]
+    f["a3"] = np.reciprocal(s, out=s)
+    kk = np.arange(k0, k1, dtype=np.float64) / float(K - 1)
+    noise = f.pop("pnoise")
+    noise += (kk * kk)[:, None, None]
+    f["p"] = noise
+    f["bnd"] = interior_mask(I, J, K)[k0:k1, j0:j1, i0:i1].copy() if N <= 1 << 22 else _box_mask(I, J, K, lo, hi)
+    return {name: f[name] for name in FIELD_NAMES}
+
+
+def _box_mask(I, J, K, lo, hi):
+    """interior_mask(I, J, K) on the box lo <= (i, j, k) < hi, without the full array."""
+    i = np.arange(lo[0], hi[0])
+    j = np.arange(lo[1], hi[1])
+    k = np.arange(lo[2], hi[2])
+    mi = ((i >= 1) & (i <= I - 2)).astype(np.float64)
+    mj = ((j >= 1) & (j <= J - 2)).astype(np.float64)
+    mk = ((k >= 1) & (k <= K - 2)).astype(np.float64)
+    return mk[:, None, None] * mj[None, :, None] * mi[None, None, :]
+
+
+def target_field_box(I: int, J: int, K: int, lo, hi, seed: int = TARGET_SEED) -> np.ndarray:
+    """target_field(I, J, K) restricted to the box lo <= (i, j, k) < hi."""
+    out = np.zeros((hi[2] - lo[2], hi[1] - lo[1], hi[0] - lo[0]), dtype=np.float64)
+    ii = np.arange(lo[0], hi[0], dtype=np.float64)
+    jj = np.arange(lo[1], hi[1], dtype=np.float64)
+    kk = np.arange(lo[2], hi[2], dtype=np.float64)
+    for l, m, n in target_modes(seed):
+        si = np.sin(np.pi * l * ii / (I - 1))
+        sj = np.sin(np.pi * m * jj / (J - 1))
+        sk = np.sin(np.pi * n * kk / (K - 1))
+        out += 0.1 * sk[:, None, None] * sj[None, :, None] * si[None, None, :]
+    return out
+
+
 def batch_dims(n_grids: int, seed: int = BATCH_DIMS_SEED) -> list[tuple[int, int, int]]:
     """(I, J, K) of each batch grid: three draws per grid, each picks one of
     BATCH_DIM_CHOICES uniformly as floor(6u)."""

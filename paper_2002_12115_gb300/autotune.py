@@ -230,10 +230,11 @@ class PlanGenome:
 
 
 def ga_search(n_bits: int, measure, M: int = 10, T: int = 10, pc: float = GA_PC, pm: float = GA_PM,
-              seed: int = 0, log=None):
+              seed: int = 0, log=None, on_generation=None):
     """Minimise measure(bits) -> seconds (None or inf = failed run) with the
     paper's GA.  Returns (best_bits, best_time, history); history holds the
-    best time of every generation and the number of distinct measurements."""
+    best time of every generation and the number of distinct measurements.
+    on_generation(gen, population, times), if given, sees every generation."""
     import numpy as np
     rng = np.random.default_rng(seed)
     cache: dict = {}
@@ -250,6 +251,8 @@ def ga_search(n_bits: int, measure, M: int = 10, T: int = 10, pc: float = GA_PC,
     best = None
     for gen in range(T):
         times = np.array([time_of(ind) for ind in pop])
+        if on_generation:
+            on_generation(gen, list(pop), times.copy())
         fit = times ** -0.5
         order = np.argsort(times)
         if best is None or times[order[0]] < best[1]:
@@ -308,3 +311,108 @@ def ga_tune_batch(batch, M: int = 10, T: int = 10, n_sweeps: int = 10, reps: int
     plan["s_per_sweep"] = t / n_sweeps
     plan["history"] = history
     return plan
+
+
+# --------------------------------------------------------------------------
+# Exhaustive baselines for the searches above.
+
+def _default_plan(dims, widths, warps=8, kdepth=16) -> dict:
+    """The starting plan of the coordinate descent: the widest tile that
+    wastes the fewest lanes per I class, one k-depth for every K class."""
+    return {"warps": warps,
+            "tile_i": {str(I): min(widths, key=lambda t: (((I - 2) // t + 1) * t, -t))
+                       for I in sorted({d[0] for d in dims})},
+            "kdepth": {str(K): kdepth for K in sorted({d[2] for d in dims})}}
+
+
+def _batch_measure(batch, n_sweeps, reps):
+    dims = batch.dims
+
+    def expand(plan):
+        ti = [plan["tile_i"][str(I)] for I, _, _ in dims]
+        kd = [min(plan["kdepth"][str(K)], max(K - 2, 1)) for _, _, K in dims]
+        return ti, kd
+
+    def measure(plan) -> float:
+        ti, kd = expand(plan)
+        try:
+            batch.set_plan(plan["warps"], ti, kd)
+            batch.sweep(n_sweeps, residuals=False)
+        except JacError:
+            return float("inf")
+        return time_call(lambda: batch.sweep(n_sweeps, residuals=False), reps)
+    return measure, expand
+
+
+def class_exhaustive_tune_batch(batch, n_sweeps: int = 10, reps: int = 2, kdepths=(4, 8, 16, 32, 64, 12, 24, 48),
+                                warps=(8, 4), log=None) -> dict:
+    """Exhaustive search per size class: for each warp count, every tile
+    width of each I class and every k-depth of each K class is measured with
+    all other classes at the default plan; the per-class best choices are
+    combined into one plan, which is measured too.  Exact when the batch's
+    time is a sum of per-class terms; it measures warps x (widths x I classes
+    + depths x K classes) + 1 plans."""
+    dims = batch.dims
+    widths = _tile_widths(batch.prec)
+    measure, expand = _batch_measure(batch, n_sweeps, reps)
+    best_plan, best_t, count = None, float("inf"), 0
+    for w in warps:
+        base = _default_plan(dims, widths, w)
+        plan = json.loads(json.dumps(base))
+        for I in base["tile_i"]:
+            trials = []
+            for tw in widths:
+                cand = json.loads(json.dumps(base))
+                cand["tile_i"][I] = tw
+                trials.append((measure(cand), tw))
+                count += 1
+            plan["tile_i"][I] = min(trials)[1]
+        for K in base["kdepth"]:
+            trials = []
+            for kd in kdepths:
+                if kd > max(int(K) - 2, 1):
+                    continue
+                cand = json.loads(json.dumps(base))
+                cand["kdepth"][K] = kd
+                trials.append((measure(cand), kd))
+                count += 1
+            plan["kdepth"][K] = min(trials)[1]
+        t = measure(plan)
+        count += 1
+        if log:
+            log(f"warps {w}: combined per-class plan {t / n_sweeps * 1e3:.3f} ms/sweep")
+        if t < best_t:
+            best_plan, best_t = plan, t
+    ti, kd = expand(best_plan)
+    batch.set_plan(best_plan["warps"], ti, kd)
+    best_plan = dict(best_plan, s_per_sweep=best_t / n_sweeps, measured=count)
+    return best_plan
+
+
+def joint_exhaustive_tune_batch(batch, n_sweeps: int = 5, reps: int = 2, kdepths=(4, 8, 16, 32, 64, 12, 24, 48),
+                                warps=(8,), max_plans: int = 4096, log=None) -> dict:
+    """Every plan of the batch's plan space (all tile widths of every I class
+    times all k-depths of every K class, for each warp count): the true
+    optimum the heuristic searches are judged against.  Only for small
+    batches (at most max_plans plans)."""
+    dims = batch.dims
+    widths = _tile_widths(batch.prec)
+    i_cl = [str(I) for I in sorted({d[0] for d in dims})]
+    k_cl = [str(K) for K in sorted({d[2] for d in dims})]
+    k_opts = [[kd for kd in kdepths if kd <= max(int(K) - 2, 1)] or [1] for K in k_cl]
+    space = list(product(warps, product(widths, repeat=len(i_cl)), product(*k_opts)))
+    if len(space) > max_plans:
+        raise ValueError(f"{len(space)} plans: too many for an exhaustive search")
+    measure, expand = _batch_measure(batch, n_sweeps, reps)
+    results = []
+    for w, tws, kds in space:
+        plan = {"warps": w, "tile_i": dict(zip(i_cl, tws)), "kdepth": dict(zip(k_cl, kds))}
+        results.append((measure(plan), plan))
+    results.sort(key=lambda r: r[0])
+    t, plan = results[0]
+    ti, kd = expand(plan)
+    batch.set_plan(plan["warps"], ti, kd)
+    if log:
+        log(f"{len(results)} plans: best {t / n_sweeps * 1e3:.3f} ms/sweep")
+    return dict(plan, s_per_sweep=t / n_sweeps, measured=len(results),
+                times=sorted(r[0] / n_sweeps for r in results))

@@ -102,3 +102,19 @@ def test_torch_generator_is_bit_identical():
     u = ji.uniform(123, 1000, 5000, -1.0, 1.0)
     v = ji.uniform_torch(123, 1000, 5000, -1.0, 1.0, device="cpu", chunk=777).numpy()
     assert np.array_equal(u, v)
+
+
+def test_box_generation_equals_slices_of_the_full_grid():
+    """himeno_fields_box and target_field_box draw a sub-box of a grid
+    directly; they equal, bitwise, the same box cut from the full arrays
+    (faces and interior both)."""
+    I, J, K = 23, 17, 19
+    full = ji.himeno_fields(I, J, K, seed=77)
+    tfull = ji.target_field(I, J, K)
+    for lo, hi in (((0, 0, 0), (5, 4, 3)), ((7, 3, 11), (23, 17, 19)), ((1, 1, 1), (22, 16, 18))):
+        box = ji.himeno_fields_box(I, J, K, lo, hi, seed=77)
+        sl = (slice(lo[2], hi[2]), slice(lo[1], hi[1]), slice(lo[0], hi[0]))
+        for name in ji.FIELD_NAMES:
+            assert np.array_equal(box[name], full[name][sl]), name
+        assert np.array_equal(ji.target_field_box(I, J, K, lo, hi), tfull[sl])
+        assert np.array_equal(ji._box_mask(I, J, K, lo, hi), full["bnd"][sl])
