@@ -447,11 +447,24 @@ jac_status launch_pass_t(int N, const PassArgs &a, unsigned grid, unsigned block
         return JAC_EINVAL;
     }
     smem = (smem + 15) / 16 * 16;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) {
-            jac::set_thread_error(std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
-            return JAC_ECUDA;
+    // opt in to more than the default dynamic shared memory (the kernel's
+    // static reduction buffer counts against the same 48 KB); once per
+    // kernel and size
+    if (smem > 32 * 1024) {
+        static std::mutex mu;
+        static std::vector<std::pair<const void *, size_t>> done;
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = std::find_if(done.begin(), done.end(), [&](const std::pair<const void *, size_t> &d) {
+            return d.first == (const void *)kern;
+        });
+        if (it == done.end() || it->second < smem) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) {
+                jac::set_thread_error(std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+                return JAC_ECUDA;
+            }
+            if (it == done.end()) done.emplace_back((const void *)kern, smem);
+            else it->second = smem;
         }
     }
     kern<<<grid, block, smem, st>>>(a);
