@@ -69,6 +69,7 @@ WORKLOADS = {
     "batch-f64": dict(n_grids=512, sweeps=100, prec="f64"),
     "tuners": dict(n_grids=512, sweeps=100, prec="f32"),
     "oracle-configs": dict(),
+    "sweep-latency": dict(I=33, J=33, K=65, sweeps=200, prec="f64"),
     "adjoint": dict(I=513, J=513, K=1025, sweeps=100, taped=20, C=5, prec="f32"),
     "adjoint-medium": dict(I=257, J=257, K=513, sweeps=40, taped=20, C=5, prec="f32"),
     "adjoint-65": dict(I=65, J=65, K=129, sweeps=50, taped=50, C=10, prec="f64"),
@@ -851,6 +852,42 @@ def bench_fft(args, w, stream, steps=None, warmup=None, e2e=True, parity=True):
     return out
 
 
+def bench_sweep_latency(w, stream):
+    """Per-sweep cost of one launch on a small grid: launches of n = 1 .. 200
+    sweeps timed with CUDA events (median of 5), fitted as time = a + b n
+    (a: launch and ring start-up, b: one sweep including its grid barrier),
+    for the default plan and for plans that give the launch fewer or more
+    CTAs (k-depth), and the FP64 arithmetic floor of one sweep."""
+    import numpy as np
+    import torch
+
+    from paper_2002_12115_gb300 import Jacobi, resolve_plan
+    from paper_2002_12115_gb300 import autotune as at
+    I, J, K, prec = w["I"], w["J"], w["K"], w["prec"]
+    dev = device_fields(I, J, K)
+    out = {"grid": [I, J, K], "prec": prec}
+    ns = [1, 2, 5, 10, 50, 100, 200]
+    plans = {"default": (0, 0, 0)}
+    for kd in (1, 2, 4, 8, 16, 32, 63):
+        plans[f"kdepth {kd}"] = (0, kd, 0)
+    with Jacobi(I, J, K, prec, 0.8, stream) as jac:
+        jac.upload_tensors(dev)
+        for name, plan in plans.items():
+            jac.set_plan(*plan)
+            jac.sweep(3)
+            jac.residual()
+            ts = [at.time_call(lambda: jac.sweep(n), 5, stream) * 1e6 for n in ns]
+            b, a = np.polyfit(ns, ts, 1)
+            rp = resolve_plan(I, J, K, prec, tile_j=plan[0], kdepth=plan[1], tile_i=plan[2])
+            ti, tj, kd = rp["tile_i"], rp["tile_j"], rp["kdepth"]
+            items = ((I - 2) // ti + 1) * (-(-(J - 2) // tj)) * (-(-(K - 2) // kd) if kd > 0 else 1)
+            out[name] = {"us_per_sweep": b, "launch_us": a, "plan": rp, "work_items": items,
+                         "us_at": dict(zip(ns, ts))}
+    nint = (I - 2) * (J - 2) * (K - 2)
+    out["fp64_alu_floor_us_per_sweep"] = nint * F64_OPS_PER_POINT / (f64_alu_peak_gops() * 1e9) * 1e6
+    return out
+
+
 def run_native(args, w, wname):
     import torch
 
@@ -898,6 +935,12 @@ def run_native(args, w, wname):
                      "config": {"workload": "512 grids, dims drawn from {17,33,49,65,97,129}, f32, 100 sweeps; "
                                             "plans searched from scratch"},
                      "searches": r})
+    if wname == "sweep-latency":
+        r = bench_sweep_latency(w, stream)
+        return emit({"metric": "19-pt Jacobi per-sweep latency (us) on a small grid", "value": r["default"]["us_per_sweep"],
+                     "unit": "us per sweep", "higher_is_better": False, "n_gpus": world, "dtype": w["prec"],
+                     "data": "synthetic", "config": {"workload": f"{w['I']}x{w['J']}x{w['K']} {w['prec']}, launches "
+                                                                "of 1..200 sweeps"}, "latency": r})
     if wname.startswith("fft"):
         r = bench_fft(args, w, stream, parity=not args.no_parity, e2e=not args.no_e2e)
         ms = max_over_ranks(r["ms_per_step"], args.dist)

@@ -166,8 +166,10 @@ struct PassArgs {
     int axis;                // 0: x, 1: y, 2: z
     int W;                   // lines per CTA
     double scale;            // applied by the last stage (1 or 1/N)
-    double c;                // spectral factor exp(c |kbar|^2) applied on load; used when factor != 0
-    int factor;
+    int factor;              // multiply by the spectral factor on load (first pass of a step)
+    const void *fa;          // factor tables exp(c kbar^2) (element type T): this pass's axis,
+    const void *fb;          // and the line's other two axes (for the pass along x: y, then z)
+    const void *fc;
     double *partials;        // per-CTA sums of |u|^2 (energy != NULL)
     unsigned *counter;       // CTAs done (last one reduces and resets it)
     double *energy;
@@ -177,6 +179,18 @@ __device__ __forceinline__ double kbar2(int k, int n)
 {
     const int s = k < (n + 1) / 2 ? k : k - n;
     return (double)s * (double)s;
+}
+
+// The spectral factor along each axis, exp(c kbar^2) for every index of
+// n1, then n2, then n3 (FP64 exp, stored as T): one small launch per step,
+// so that a pass multiplies by a table entry per element and one per line.
+template <typename T>
+__global__ void k_fft_factors(double c, int n1, int n2, int n3, T *f1, T *f2, T *f3)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n1) f1[i] = (T)exp(c * kbar2(i, n1));
+    else if (i < n1 + n2) f2[i - n1] = (T)exp(c * kbar2(i - n1, n2));
+    else if (i < n1 + n2 + n3) f3[i - n1 - n2] = (T)exp(c * kbar2(i - n1 - n2, n3));
 }
 
 // One Stockham stage for the BPT = RMAX / R butterflies of this thread.
@@ -282,11 +296,14 @@ __global__ void __launch_bounds__(512) k_fft_pass(const PassArgs a)
 
     // twiddles (and the spectral factor along this axis) into shared memory
     const C2<T> *gtw = static_cast<const C2<T> *>(a.tw);
+    const T *gfa = static_cast<const T *>(a.fa);
     for (int m = threadIdx.x; m < N; m += blockDim.x) {
         if constexpr (RX::R2 > 1) tw[m] = gtw[m];
-        if (a.factor) fe[m] = (T)exp(a.c * kbar2(m, N));
+        if (a.factor) fe[m] = gfa[m];
     }
-    if (a.factor && t == 0) fl[w] = (T)exp(a.c * (kbar2(ia, na) + kbar2(ib, nb)));
+    if (a.factor && t == 0) fl[w] = static_cast<const T *>(a.fb)[ia] * static_cast<const T *>(a.fc)[ib];
+    (void)na;
+    (void)nb;
     __syncthreads();
 
     const C2<T> *gin = static_cast<const C2<T> *>(a.in);
@@ -388,6 +405,7 @@ int threads_of_pass(int N, int W) { return (N / rmax_of(N)) * W; }
 
 struct Layout {
     size_t tw[3];       // offsets of the twiddle tables
+    size_t fac[3];      // offsets of the spectral factor tables
     size_t partials;
     size_t total;
     long long max_ctas;
@@ -400,6 +418,10 @@ Layout layout(const int n[3], jfft_prec prec)
     for (int a = 0; a < 3; ++a) {
         L.tw[a] = off;
         off += round256((size_t)n[a] * elem_bytes(prec));
+    }
+    for (int a = 0; a < 3; ++a) {
+        L.fac[a] = off;
+        off += round256((size_t)n[a] * elem_bytes(prec) / 2);
     }
     L.max_ctas = 0;
     for (int a = 0; a < 3; ++a)
@@ -515,6 +537,19 @@ jac_status run3(jfft_plan *p, const void *in, void *out, bool inv, double scale,
         const char *a = static_cast<const char *>(in), *b = static_cast<const char *>(out);
         if (a < b + bytes && b < a + bytes) return plan_fail(p, JAC_EINVAL, "in and out overlap without being equal");
     }
+    if (factor) {
+        const int nt = p->n[0] + p->n[1] + p->n[2];
+        if (p->prec == JFFT_C32)
+            jfft::k_fft_factors<float><<<(nt + 255) / 256, 256, 0, p->stream>>>(
+                c, p->n[0], p->n[1], p->n[2], reinterpret_cast<float *>(p->ws + p->L.fac[0]),
+                reinterpret_cast<float *>(p->ws + p->L.fac[1]), reinterpret_cast<float *>(p->ws + p->L.fac[2]));
+        else
+            jfft::k_fft_factors<double><<<(nt + 255) / 256, 256, 0, p->stream>>>(
+                c, p->n[0], p->n[1], p->n[2], reinterpret_cast<double *>(p->ws + p->L.fac[0]),
+                reinterpret_cast<double *>(p->ws + p->L.fac[1]), reinterpret_cast<double *>(p->ws + p->L.fac[2]));
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return plan_fail(p, JAC_ECUDA, std::string("factor launch: ") + cudaGetErrorString(e));
+    }
     for (int axis = 0; axis < 3; ++axis) {
         const int N = p->n[axis];
         jfft::PassArgs a;
@@ -527,7 +562,9 @@ jac_status run3(jfft_plan *p, const void *in, void *out, bool inv, double scale,
         a.W = jfft::lines_per_cta(axis, N, p->n, p->prec);
         a.scale = axis == 2 ? scale : 1.0;
         a.factor = (factor && axis == 0) ? 1 : 0;
-        a.c = c;
+        a.fa = p->ws + p->L.fac[0];
+        a.fb = p->ws + p->L.fac[1];
+        a.fc = p->ws + p->L.fac[2];
         if (axis == 2 && energy) {
             a.energy = energy;
             a.partials = reinterpret_cast<double *>(p->ws + p->L.partials);
@@ -582,7 +619,7 @@ jac_status jfft_plan_create(jfft_plan **out, int n1, int n2, int n3, jfft_prec p
     p->ws = static_cast<char *>(workspace);
     p->L = L;
     // twiddle tables W_N^m = exp(-2 pi i m / N), in FP64 on the host, stored in the plan's precision
-    std::vector<unsigned char> host(L.partials - 256, 0);
+    std::vector<unsigned char> host(L.fac[0] - 256, 0);
     const double pi = 3.14159265358979323846264338327950288;
     for (int a = 0; a < 3; ++a) {
         unsigned char *dst = host.data() + (L.tw[a] - 256);
