@@ -417,12 +417,9 @@ def bench_single(args, w, stream):
     dev = device_fields(I, J, K)
     host = None
     if args.need_host:
-        # pinned host copies of the same inputs (bitwise those of the numpy
+        # host copies of the same inputs (bitwise those of the numpy
         # generator), for the end-to-end steps and the oracle
-        host = {}
-        for k, v in dev.items():
-            host[k] = torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
-            host[k].copy_(v)
+        host = {k: v.cpu() for k, v in dev.items()}
     p_dev = torch.empty((K, J, I), dtype=torch.float64, device="cuda")
     jac = Jacobi(I, J, K, prec, 0.8, stream)
     if args.tile_j or args.kdepth or args.tile_i or args.fuse:
@@ -457,10 +454,12 @@ def bench_single(args, w, stream):
             "residual": gosa, "jac": jac, "dev": dev, "host": host, "p": p_dev, "clocks": clk.summary()}
 
 
-def bench_e2e(args, w, jac, stream, want_residual, host_t):
-    """The same step through the C ABI from pinned host FP64 buffers: every
-    step copies its thirteen inputs in, sweeps, and copies the state and the
-    residual out, all inside the timed region.  Two contexts on two streams
+def bench_e2e(args, w, jac, stream, want_residual, host_t, f32_host=False):
+    """The same step through the C ABI from pinned host buffers: every step
+    copies its thirteen inputs in, sweeps, and copies the state and the
+    residual out, all inside the timed region.  f32_host: the inputs as FP32
+    host arrays (jac_upload_f32_async / jac_download_f32_async; the numbers
+    an FP32-stored problem holds), else FP64.  Two contexts on two streams
     take the steps in turn: one step's host-to-device copies run on the copy
     engine while the previous step's sweeps hold the SMs, and the previous
     step's results are copied out while this step sweeps."""
@@ -474,8 +473,21 @@ def bench_e2e(args, w, jac, stream, want_residual, host_t):
     def pinned(shape):
         return torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
 
-    host = {k: v.numpy() for k, v in host_t.items()}     # pinned FP64 inputs
-    p_host = [pinned((K, J, I)) for _ in range(2)]
+    if f32_host:
+        # the inputs as FP32 numbers (what FP32 storage holds), in pinned memory
+        host = {}
+        for k, v in host_t.items():
+            t = torch.empty(v.shape, dtype=torch.float32, pin_memory=True)
+            t.copy_(v)
+            host[k] = t.numpy()
+        p_host = [torch.empty((K, J, I), dtype=torch.float32, pin_memory=True).numpy() for _ in range(2)]
+    else:
+        host = {}
+        for k, v in host_t.items():                          # pinned FP64 inputs
+            t = torch.empty(v.shape, dtype=torch.float64, pin_memory=True)
+            t.copy_(v)
+            host[k] = t.numpy()
+        p_host = [pinned((K, J, I)) for _ in range(2)]
     res_host = [pinned((1,)) for _ in range(2)]
     stream2 = torch.cuda.Stream()
     jac2 = Jacobi(I, J, K, w["prec"], 0.8, stream2, async_upload=True)
@@ -484,18 +496,21 @@ def bench_e2e(args, w, jac, stream, want_residual, host_t):
     ctxs = (jac, jac2)
     residuals = []
 
+    up = (lambda c: c.upload_f32_async(host)) if f32_host else (lambda c: c.upload_async(host))
+    down = (lambda c, o, r: c.download_f32_async(o, r)) if f32_host else (lambda c, o, r: c.download_async(o, r))
+
     def run(steps):
         for k in range(steps):
             cur, prev = ctxs[k % 2], ctxs[(k - 1) % 2]
-            cur.upload_async(host)
+            up(cur)
             if k >= 1:                       # the previous step's results, behind its sweeps
-                prev.download_async(p_host[(k - 1) % 2], res_host[(k - 1) % 2])
+                down(prev, p_host[(k - 1) % 2], res_host[(k - 1) % 2])
             cur.sweep(n)
             if k >= 1:
                 prev.sync()
                 residuals.append(float(res_host[(k - 1) % 2][0]))
         last = ctxs[(steps - 1) % 2]
-        last.download_async(p_host[(steps - 1) % 2], res_host[(steps - 1) % 2])
+        down(last, p_host[(steps - 1) % 2], res_host[(steps - 1) % 2])
         last.sync()
         residuals.append(float(res_host[(steps - 1) % 2][0]))
 
@@ -509,12 +524,13 @@ def bench_e2e(args, w, jac, stream, want_residual, host_t):
     ms = (time.perf_counter() - t0) * 1e3
     jac2.close()
     # same inputs and a bitwise-reproducible sweep: every step's residual is
-    # the same, and (host and device input generators) that of the
-    # device-resident run within the FP32 state's rounding
+    # the same, and that of the device-resident run (for FP32 host arrays the
+    # stored values are the same numbers, so bitwise too)
     if len(set(residuals)) != 1 or not abs(residuals[0] - want_residual) <= 1e-5 * abs(want_residual):
         raise RuntimeError(f"end-to-end residuals {sorted(set(residuals))} against the device-resident "
                            f"run's {want_residual}")
-    return ms, host
+    del host, p_host
+    return ms
 
 
 def bench_unhoisted_grid(w, sweeps=20):
@@ -977,8 +993,9 @@ def run_native(args, w, wname):
     units = n_interior(w) * n * args.steps / 1e9
     value, ms = replica_value(units, s["ms"], world, args.dist)
     e2e = None
+    f32_host = prec != "f64"
     if not args.no_e2e:
-        e2e_ms, _ = bench_e2e(args, w, s["jac"], stream, s["residual"], s["host"])
+        e2e_ms = bench_e2e(args, w, s["jac"], stream, s["residual"], s["host"], f32_host=f32_host)
         e2e, e2e_ms = replica_value(units, e2e_ms, world, args.dist)
     p_gpu = s["p"].cpu().numpy()          # state after the last timed step
     gosa = s["residual"]
@@ -1054,10 +1071,12 @@ def run_native(args, w, wname):
         "cpu_baseline": cpu,
         "parity": parity,
         "e2e": None if e2e is None else {
-            "value": e2e, "unit": UNIT, "h2d_bytes_per_step": 13 * I * J * K * 8,
-            "d2h_bytes_per_step": I * J * K * 8 + 8,
-            "how": "jac_upload_async from pinned host FP64 arrays, jac_sweep, jac_download_async of the "
-                   "state and the residual, jac_sync; two contexts on two streams take the steps in turn"},
+            "value": e2e, "unit": UNIT, "h2d_bytes_per_step": 13 * I * J * K * (4 if f32_host else 8),
+            "d2h_bytes_per_step": I * J * K * (4 if f32_host else 8) + 8,
+            "how": (f"jac_upload_{'f32_' if f32_host else ''}async from pinned host "
+                    f"{'FP32' if f32_host else 'FP64'} arrays (the inputs of the {prec} problem), jac_sweep, "
+                    f"jac_download_{'f32_' if f32_host else ''}async of the state and the residual, jac_sync; "
+                    "two contexts on two streams take the steps in turn")},
         "gpu_launches": args.steps * 15,
         "clocks": s["clocks"],
         "residual": gosa,

@@ -82,6 +82,12 @@ typedef struct jac_fields {
     const double *f[JAC_NFIELDS];
 } jac_fields;
 
+/* The same thirteen arrays as dense FP32 values (host memory), for problems
+ * whose inputs are FP32 numbers. */
+typedef struct jac_fields_f32 {
+    const float *f[JAC_NFIELDS];
+} jac_fields_f32;
+
 /* Storage pitch (elements) of every array of an I-wide grid: I rounded up to
  * a multiple of 8, so that each row starts on a 16-byte boundary in every
  * element type (the TMA stride rule) and vector loads stay aligned. */
@@ -320,6 +326,16 @@ jac_status jac_upload(jac_ctx *ctx, const jac_fields *host);
  * allocated. */
 jac_status jac_upload_async(jac_ctx *ctx, const jac_fields *host);
 
+/* jac_upload_async for inputs that are FP32 numbers, as dense FP32 host
+ * arrays: half the host-to-device bytes of the FP64 form (52 instead of 104
+ * bytes per point), the same transfer hoisting (Section 3.2-3.3).  FP64 and
+ * FP32 storage keep each value; BF16-stored coefficients are its RNE
+ * rounding -- for FP64 inputs that are FP32 numbers, exactly the storage
+ * values jac_upload_async gives.  Uses the same staging arrays (a borrowed
+ * context needs async_upload in its workspace spec).  Errors: as
+ * jac_upload_async. */
+jac_status jac_upload_f32_async(jac_ctx *ctx, const jac_fields_f32 *host);
+
 /* Same as jac_upload with the thirteen arrays in device memory (dense FP64);
  * asynchronous. */
 jac_status jac_upload_dev(jac_ctx *ctx, const jac_fields *dev);
@@ -347,6 +363,11 @@ jac_status jac_download_dev(jac_ctx *ctx, double *p_dev);
  * JAC_EINVAL (NULL ctx or p_host), JAC_ESTATE (res_host given and no sweep
  * since the last upload), JAC_ECUDA. */
 jac_status jac_download_async(jac_ctx *ctx, double *p_host, double *res_host);
+
+/* jac_download_async with the state as dense FP32 (I*J*K floats): exact for
+ * FP32 state storage, RNE of the value for FP64 storage; the residual stays
+ * FP64.  Valid after jac_sync.  Errors: as jac_download_async. */
+jac_status jac_download_f32_async(jac_ctx *ctx, float *p_host, double *res_host);
 
 /* Wait for the context's stream and check the sweep workspace's error word:
  * JAC_ETIMEOUT if a bounded device wait of an earlier sweep gave up (the

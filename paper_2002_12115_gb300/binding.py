@@ -38,6 +38,10 @@ class jac_fields(ctypes.Structure):
     _fields_ = [("f", ctypes.c_void_p * NFIELDS)]
 
 
+class jac_fields_f32(ctypes.Structure):
+    _fields_ = [("f", ctypes.c_void_p * NFIELDS)]
+
+
 class jac_grid(ctypes.Structure):
     _fields_ = [("I", ctypes.c_int), ("J", ctypes.c_int), ("K", ctypes.c_int), ("prec", ctypes.c_int),
                 ("omega", ctypes.c_double), ("p", ctypes.c_void_p * 2),
@@ -81,6 +85,8 @@ _SIG = {
     "jac_upload_dev": (_I, [_VP, ctypes.POINTER(jac_fields)]),
     "jac_upload_async": (_I, [_VP, ctypes.POINTER(jac_fields)]),
     "jac_download_async": (_I, [_VP, _VP, _VP]),
+    "jac_upload_f32_async": (_I, [_VP, ctypes.POINTER(jac_fields_f32)]),
+    "jac_download_f32_async": (_I, [_VP, _VP, _VP]),
     "jac_sync": (_I, [_VP]),
     "jac_sweep": (_I, [_VP, _I]),
     "jac_residual": (_I, [_VP, ctypes.POINTER(ctypes.c_double)]),
@@ -334,6 +340,31 @@ class Jacobi:
         self._ensure_workspace(async_upload=True)
         self._check(lib().jac_upload_async(self._h, ctypes.byref(f)))
         self._pending.append(fields)
+
+    def upload_f32_async(self, fields: dict) -> None:
+        """Copy in thirteen dense FP32 host arrays (float32, shape (K, J, I))
+        without waiting: half the bytes of upload_async, for inputs that are
+        FP32 numbers.  The arrays are kept referenced until sync()."""
+        f = jac_fields_f32()
+        for q, name in enumerate(FIELDS):
+            a = fields[name]
+            if tuple(a.shape) != self.shape or a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError(f"{name}: expected a C-contiguous float32 array of shape {self.shape}")
+            f.f[q] = a.ctypes.data
+        self._ensure_workspace(async_upload=True)
+        self._check(lib().jac_upload_f32_async(self._h, ctypes.byref(f)))
+        self._pending.append(fields)
+
+    def download_f32_async(self, out: np.ndarray, res_out: np.ndarray | None = None) -> None:
+        """Enqueue the copy-out of the state as FP32 to `out` (float32, shape
+        (K, J, I)) and, if given, of the residual to res_out[0]; valid after sync()."""
+        if tuple(out.shape) != self.shape or out.dtype != np.float32 or not out.flags.c_contiguous:
+            raise ValueError(f"out: expected a contiguous float32 array of shape {self.shape}")
+        if res_out is not None and (res_out.dtype != np.float64 or res_out.size < 1):
+            raise ValueError("res_out: expected a float64 array of at least one element")
+        self._check(lib().jac_download_f32_async(self._h, _VP(out.ctypes.data),
+                                                 _VP(_host_ptr(res_out)) if res_out is not None else None))
+        self._pending.append((out, res_out))
 
     def download_async(self, out: np.ndarray, res_out: np.ndarray | None = None) -> None:
         """Enqueue the copy-out of the state to `out` (float64, shape (K, J, I))

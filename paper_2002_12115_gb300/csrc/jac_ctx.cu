@@ -241,7 +241,7 @@ jac_status sweep_impl(jac_ctx *c, int n_iter)
     return JAC_OK;
 }
 
-enum class Src { host, device, host_async };
+enum class Src { host, device, host_async, host_async_f32 };
 
 // The copy-in.  Host sources go through device staging: one array reused
 // per field (synchronous), or, for the asynchronous form, one staging array
@@ -254,9 +254,41 @@ jac_status upload_impl(jac_ctx *c, const jac_fields *f, Src from)
     for (int q = 0; q < JAC_NFIELDS; ++q)
         if (!f->f[q]) return ctx_fail(c, JAC_EINVAL, "field " + std::to_string(q) + " is NULL");
     const size_t n = (size_t)c->I * c->J * c->K;
-    if (from == Src::host_async && !c->stage_all && c->borrowed)
+    const bool async = from == Src::host_async || from == Src::host_async_f32;
+    if (async && !c->stage_all && c->borrowed)
         return ctx_fail(c, JAC_ENOMEM, "the borrowed workspace has no room for the asynchronous staging arrays "
                                        "(jac_set_workspace with async_upload set)");
+    if (from == Src::host_async_f32) {
+        // thirteen FP32 copies into the asynchronous staging (as floats), then the packing kernels
+        const float *const *src32 = reinterpret_cast<const float *const *>(f->f);
+        if (!c->stage_all) {
+            cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&c->stage_all), JAC_NFIELDS * n * sizeof(double));
+            if (e != cudaSuccess) {
+                c->stage_all = nullptr;
+                return ctx_fail(c, JAC_ENOMEM, "device allocation of the asynchronous staging arrays failed");
+            }
+        }
+        float *st32 = reinterpret_cast<float *>(c->stage_all);
+        for (int q = 0; q < JAC_NFIELDS; ++q) {
+            cudaError_t e = cudaMemcpyAsync(st32 + (size_t)q * n, src32[q], n * sizeof(float), cudaMemcpyHostToDevice,
+                                            c->stream);
+            if (e != cudaSuccess) return ctx_cuda(c, e, "host-to-device copy");
+        }
+        for (int q = 0; q < JAC_NFIELDS; ++q) {
+            jac_status s = jac::pack_dev_f32(c->I, c->J, c->K, c->prec, q, st32 + (size_t)q * n,
+                                             q == JAC_P ? c->pbuf[0] : c->arr[q], c->stream);
+            if (s != JAC_OK) return ctx_from_thread(c, s);
+        }
+        cudaError_t e = cudaMemcpyAsync(c->pbuf[1], c->pbuf[0], data_bytes(c, JAC_P), cudaMemcpyDeviceToDevice,
+                                        c->stream);
+        if (e != cudaSuccess) return ctx_cuda(c, e, "device copy of p0");
+        c->cur = 0;
+        c->count = 0;
+        c->uploaded = true;
+        c->has_res = false;
+        tape_free(c);
+        return JAC_OK;
+    }
     if (from == Src::host_async && !c->stage_all) {
         cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&c->stage_all), JAC_NFIELDS * n * sizeof(double));
         if (e != cudaSuccess) {
@@ -473,6 +505,14 @@ jac_status jac_upload_async(jac_ctx *c, const jac_fields *host) { return upload_
 
 jac_status jac_upload_dev(jac_ctx *c, const jac_fields *dev) { return upload_impl(c, dev, Src::device); }
 
+jac_status jac_upload_f32_async(jac_ctx *c, const jac_fields_f32 *host)
+{
+    if (!host) return ctx_fail(c, JAC_EINVAL, "fields is NULL");
+    jac_fields f;
+    for (int q = 0; q < JAC_NFIELDS; ++q) f.f[q] = reinterpret_cast<const double *>(host->f[q]);
+    return upload_impl(c, &f, Src::host_async_f32);
+}
+
 jac_status jac_sweep(jac_ctx *c, int n_iter)
 {
     if (!c) return ctx_fail(c, JAC_EINVAL, "ctx is NULL");
@@ -522,6 +562,26 @@ jac_status jac_download_async(jac_ctx *c, double *p_host, double *res_host)
     if (s != JAC_OK) return s;
     const size_t n = (size_t)c->I * c->J * c->K;
     cudaError_t e = cudaMemcpyAsync(p_host, c->staging, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return ctx_cuda(c, e, "device-to-host copy");
+    if (res_host) {
+        jac::WsHeader *hdr = static_cast<jac::WsHeader *>(c->ws);
+        e = cudaMemcpyAsync(res_host, &hdr->residual, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return ctx_cuda(c, e, "residual copy");
+    }
+    return JAC_OK;
+}
+
+jac_status jac_download_f32_async(jac_ctx *c, float *p_host, double *res_host)
+{
+    if (!c || !p_host) return ctx_fail(c, JAC_EINVAL, "NULL argument");
+    if (!c->uploaded) return ctx_fail(c, JAC_ESTATE, "download before upload");
+    if (res_host && !c->has_res) return ctx_fail(c, JAC_ESTATE, "no sweep since the last upload");
+    float *st32 = reinterpret_cast<float *>(c->staging);
+    if (!st32) return ctx_fail(c, JAC_ESTATE, "no staging array (workspace not set)");
+    jac_status s = jac::unpack_dev_f32(c->I, c->J, c->K, c->prec, JAC_P, c->pbuf[c->cur], st32, c->stream);
+    if (s != JAC_OK) return ctx_from_thread(c, s);
+    const size_t n = (size_t)c->I * c->J * c->K;
+    cudaError_t e = cudaMemcpyAsync(p_host, st32, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return ctx_cuda(c, e, "device-to-host copy");
     if (res_host) {
         jac::WsHeader *hdr = static_cast<jac::WsHeader *>(c->ws);

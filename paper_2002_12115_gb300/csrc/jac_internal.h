@@ -33,6 +33,9 @@ jac_status sweep_dev(const jac_grid *g, const jac_plan *plan, int n_iter, double
 jac_status pack_dev(int I, int J, int K, jac_prec prec, int which, const double *src, void *dst, cudaStream_t st);
 jac_status unpack_dev(int I, int J, int K, jac_prec prec, int which, const void *src, double *dst,
                       cudaStream_t st);
+jac_status pack_dev_f32(int I, int J, int K, jac_prec prec, int which, const float *src, void *dst, cudaStream_t st);
+jac_status unpack_dev_f32(int I, int J, int K, jac_prec prec, int which, const void *src, float *dst,
+                          cudaStream_t st);
 jac_status workspace_check(void *workspace, cudaStream_t st);
 int device_sm_count();
 size_t device_l2_bytes();

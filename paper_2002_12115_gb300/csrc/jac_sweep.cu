@@ -43,6 +43,41 @@ __global__ void k_pack(const double *__restrict__ src, C *__restrict__ dst, int 
     }
 }
 
+// The same from dense FP32 values (inputs that are FP32 numbers): FP64 and
+// FP32 storage keep the value, BF16 storage rounds it RNE -- the storage
+// values k_pack gives for the same numbers in FP64.
+template <typename C>
+__device__ __forceinline__ C cvt_from_f32(float x);
+template <>
+__device__ __forceinline__ double cvt_from_f32<double>(float x) { return (double)x; }
+template <>
+__device__ __forceinline__ float cvt_from_f32<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 cvt_from_f32<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+
+template <typename C>
+__global__ void k_pack_f32(const float *__restrict__ src, C *__restrict__ dst, int I, int J, int K, int pitch)
+{
+    const size_t total = (size_t)pitch * J * K;
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < total; x += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(x % (size_t)pitch);
+        const size_t row = x / (size_t)pitch;
+        dst[x] = (i < I) ? cvt_from_f32<C>(src[row * I + i]) : cvt_from_f32<C>(0.0f);
+    }
+}
+
+// Storage layout to dense FP32 (RNE from FP64 storage; exact otherwise).
+template <typename C>
+__global__ void k_unpack_f32(const C *__restrict__ src, float *__restrict__ dst, int I, int J, int K, int pitch)
+{
+    const size_t total = (size_t)I * J * K;
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < total; x += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(x % (size_t)I);
+        const size_t row = x / (size_t)I;
+        dst[x] = (float)to_f64(src[row * pitch + i]);
+    }
+}
+
 template <typename C>
 __global__ void k_unpack(const C *__restrict__ src, double *__restrict__ dst, int I, int J, int K, int pitch)
 {
@@ -224,7 +259,9 @@ int best_tile_i(int I, int J, jac_prec prec, int tj)
 //  * FP64 (bound by the FP64 pipe).  A sweep takes about rounds x (kdepth +
 //    h) plane-times, rounds = ceil(items / CTAs), h = 3 for an item's two
 //    extra state planes and its ring refill, during which the FP64 pipe
-//    idles; the smallest such cost wins (ties: the deeper item).  Balanced
+//    idles; the smallest such cost wins (ties: the deeper item); depth 1
+//    counts too (33x33x65: 126 one-plane items on 126 SMs, 6.3 us per
+//    sweep, against 9.6 us for the 64 two-plane items of depth 2).  Balanced
 //    ranges (JAC_KDEPTH_BALANCED) cost ceil(cols nk / CTAs) planes plus h
 //    for each tile a CTA's range can touch; they win where whole items
 //    leave the last round part-empty (129x129x257: 21.1 -> 22.9, and
@@ -243,9 +280,9 @@ int default_kdepth(long cols, int nk, int ctas, jac_prec prec)
         return std::min(nk, kShallow);
     }
     const long h = 3;
-    int best = 2;
+    int best = 1;
     long best_cost = -1;
-    for (int kd = 2; kd <= std::min(nk, 256); ++kd) {
+    for (int kd = 1; kd <= std::min(nk, 256); ++kd) {
         const long items = cols * ((nk + kd - 1) / kd);
         const long rounds = (items + ctas - 1) / ctas;
         const long cost = rounds * (kd + h);
@@ -534,6 +571,43 @@ jac_status pack_dev(int I, int J, int K, jac_prec prec, int which, const double 
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? JAC_OK : cuda_fail(e, "pack launch");
+}
+
+jac_status pack_dev_f32(int I, int J, int K, jac_prec prec, int which, const float *src, void *dst, cudaStream_t st)
+{
+    if (I < 3 || J < 3 || K < 3 || which < 0 || which >= JAC_NFIELDS || !src || !dst)
+        return fail(JAC_EINVAL, "bad pack arguments");
+    const int pitch = jac_pitch(I);
+    const size_t total = (size_t)pitch * J * K;
+    const int threads = 256;
+    const unsigned blocks = (unsigned)std::min<size_t>((total + threads - 1) / threads, (size_t)num_sms() * 32);
+    switch (elem_bytes(prec, which)) {
+    case 8: k_pack_f32<double><<<blocks, threads, 0, st>>>(src, static_cast<double *>(dst), I, J, K, pitch); break;
+    case 4: k_pack_f32<float><<<blocks, threads, 0, st>>>(src, static_cast<float *>(dst), I, J, K, pitch); break;
+    default:
+        k_pack_f32<__nv_bfloat16><<<blocks, threads, 0, st>>>(src, static_cast<__nv_bfloat16 *>(dst), I, J, K, pitch);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? JAC_OK : cuda_fail(e, "pack launch");
+}
+
+jac_status unpack_dev_f32(int I, int J, int K, jac_prec prec, int which, const void *src, float *dst, cudaStream_t st)
+{
+    if (I < 3 || J < 3 || K < 3 || which < 0 || which >= JAC_NFIELDS || !src || !dst)
+        return fail(JAC_EINVAL, "bad unpack arguments");
+    const int pitch = jac_pitch(I);
+    const size_t total = (size_t)I * J * K;
+    const int threads = 256;
+    const unsigned blocks = (unsigned)std::min<size_t>((total + threads - 1) / threads, (size_t)num_sms() * 32);
+    switch (elem_bytes(prec, which)) {
+    case 8: k_unpack_f32<double><<<blocks, threads, 0, st>>>(static_cast<const double *>(src), dst, I, J, K, pitch); break;
+    case 4: k_unpack_f32<float><<<blocks, threads, 0, st>>>(static_cast<const float *>(src), dst, I, J, K, pitch); break;
+    default:
+        k_unpack_f32<__nv_bfloat16>
+            <<<blocks, threads, 0, st>>>(static_cast<const __nv_bfloat16 *>(src), dst, I, J, K, pitch);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? JAC_OK : cuda_fail(e, "unpack launch");
 }
 
 jac_status unpack_dev(int I, int J, int K, jac_prec prec, int which, const void *src, double *dst, cudaStream_t st)

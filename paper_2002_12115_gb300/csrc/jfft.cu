@@ -139,6 +139,19 @@ struct Radix {
     static_assert(R1 * R2 * R3 == N, "radix plan");
 };
 
+// Elements of a line each thread holds.  The pass along x keeps the
+// largest radix (more lanes along each row); the passes along y and z take
+// up to 32 (FP32) or 16 (FP64) so that fewer threads serve a line and a CTA
+// of at most 512 threads covers 256 bytes of consecutive x.
+template <typename T, int N, bool YZ>
+__host__ __device__ constexpr int elems_per_thread()
+{
+    constexpr int rmax = Radix<N>::RMAX;
+    constexpr int cap = sizeof(T) == 4 ? 32 : 16;
+    constexpr int want = N / 16 > rmax ? N / 16 : rmax;
+    return YZ ? (want < cap ? want : cap) : rmax;
+}
+
 // Shared-memory index of element e of a line: one pad element after every
 // 16 (FP32) or 8 (FP64) elements, so that butterfly writes at stride R do
 // not fall on one bank.
@@ -256,11 +269,11 @@ __device__ __forceinline__ void stage(C2<T> (&v)[RMAX], C2<T> *tile, const C2<T>
     if constexpr (!LAST) __syncthreads();
 }
 
-template <typename T, int N, bool INV>
+template <typename T, int N, bool INV, bool YZ>
 __global__ void __launch_bounds__(512) k_fft_pass(const PassArgs a)
 {
     using RX = Radix<N>;
-    constexpr int RMAX = RX::RMAX;
+    constexpr int RMAX = elems_per_thread<T, N, YZ>();   // elements per thread
     constexpr int TT = N / RMAX;
     constexpr int RS = row_stride<T, N>();
     extern __shared__ __align__(16) unsigned char jfft_smem[];
@@ -354,18 +367,33 @@ __global__ void __launch_bounds__(512) k_fft_pass(const PassArgs a)
         s_last = atomicAdd(a.counter, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (s_last && threadIdx.x == 0) {
+    if (s_last) {
+        // every thread sums the partials b = tid, tid + blockDim, ... in
+        // order (Neumaier), then thread 0 adds those sums in thread order:
+        // a fixed order for a given launch shape
         __threadfence();
         double s = 0.0, comp = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) {     // Neumaier, in CTA order
+#pragma unroll 4
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
             const double x = __ldcg(&a.partials[b]);
             const double tsum = s + x;
             comp += fabs(s) >= fabs(x) ? (s - tsum) + x : (x - tsum) + s;
             s = tsum;
         }
-        *a.energy = s + comp;
-        *a.counter = 0u;
-        __threadfence();
+        red[threadIdx.x] = s + comp;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double e = 0.0, ec = 0.0;
+            for (unsigned i = 0; i < blockDim.x; ++i) {
+                const double x = red[i];
+                const double tsum = e + x;
+                ec += fabs(e) >= fabs(x) ? (e - tsum) + x : (x - tsum) + e;
+                e = tsum;
+            }
+            *a.energy = e + ec;
+            *a.counter = 0u;
+            __threadfence();
+        }
     }
 }
 
@@ -385,14 +413,23 @@ int rmax_of(int N)
     return (N == 32 || N == 64 || N == 512) ? 8 : 16;
 }
 
+// Elements per thread (elems_per_thread<T, N, YZ> on the host).
+int elems_of(int N, jfft_prec prec, bool yz)
+{
+    const int rmax = rmax_of(N);
+    if (!yz) return rmax;
+    const int cap = prec == JFFT_C64 ? 16 : 32;
+    return std::min(std::max(N / 16, rmax), cap);
+}
+
 // Lines per CTA of a pass (see the kernel's mapping): rows of about 256
-// threads for the pass along x; for y and z, 128 bytes of consecutive x
-// (16 FP32 or 8 FP64 complex values), at most 512 threads.
+// threads for the pass along x; for y and z, 256 bytes of consecutive x
+// (32 FP32 or 16 FP64 complex values), at most 512 threads.
 int lines_per_cta(int axis, int N, const int n[3], jfft_prec prec)
 {
-    const int tt = N / rmax_of(N);
+    const int tt = N / elems_of(N, prec, axis != 0);
     if (axis == 0) return std::max(1, std::min(256 / tt, n[1] * n[2]));
-    return std::max(1, std::min(std::min(prec == JFFT_C64 ? 8 : 16, n[0]), 512 / tt));
+    return std::max(1, std::min(std::min(prec == JFFT_C64 ? 16 : 32, n[0]), 512 / tt));
 }
 
 long long ctas_of_pass(int axis, const int n[3], int W)
@@ -401,7 +438,7 @@ long long ctas_of_pass(int axis, const int n[3], int W)
     return (long long)(n[0] / W) * (axis == 1 ? n[2] : n[1]);
 }
 
-int threads_of_pass(int N, int W) { return (N / rmax_of(N)) * W; }
+int threads_of_pass(int N, int W, jfft_prec prec, bool yz) { return (N / elems_of(N, prec, yz)) * W; }
 
 struct Layout {
     size_t tw[3];       // offsets of the twiddle tables
@@ -449,7 +486,7 @@ jac_status check_shape(int n1, int n2, int n3, jfft_prec prec)
 }  // namespace
 
 // Launch of one pass: the kernel instantiation for (T, N, INV).
-template <typename T, bool INV>
+template <typename T, bool INV, bool YZ>
 jac_status launch_pass_t(int N, const PassArgs &a, unsigned grid, unsigned block, cudaStream_t st)
 {
     size_t smem = 0;
@@ -457,7 +494,7 @@ jac_status launch_pass_t(int N, const PassArgs &a, unsigned grid, unsigned block
     switch (N) {
 #define JFFT_CASE(NN)                                                                                       \
     case NN:                                                                                                \
-        kern = k_fft_pass<T, NN, INV>;                                                                      \
+        kern = k_fft_pass<T, NN, INV, YZ>;                                                                  \
         smem = (Radix<NN>::R2 > 1 ? (size_t)a.W * row_stride<T, NN>() * sizeof(C2<T>) : 0) +               \
                (size_t)NN * sizeof(C2<T>) + (size_t)NN * sizeof(T) + (size_t)a.W * sizeof(T);               \
         break;
@@ -571,14 +608,19 @@ jac_status run3(jfft_plan *p, const void *in, void *out, bool inv, double scale,
             a.counter = reinterpret_cast<unsigned *>(p->ws);
         }
         const unsigned grid = (unsigned)jfft::ctas_of_pass(axis, p->n, a.W);
-        const unsigned block = (unsigned)jfft::threads_of_pass(N, a.W);
+        const unsigned block = (unsigned)jfft::threads_of_pass(N, a.W, p->prec, axis != 0);
         jac_status s;
+        const bool yz = axis != 0;
         if (p->prec == JFFT_C32)
-            s = inv ? jfft::launch_pass_t<float, true>(N, a, grid, block, p->stream)
-                    : jfft::launch_pass_t<float, false>(N, a, grid, block, p->stream);
+            s = inv ? (yz ? jfft::launch_pass_t<float, true, true>(N, a, grid, block, p->stream)
+                          : jfft::launch_pass_t<float, true, false>(N, a, grid, block, p->stream))
+                    : (yz ? jfft::launch_pass_t<float, false, true>(N, a, grid, block, p->stream)
+                          : jfft::launch_pass_t<float, false, false>(N, a, grid, block, p->stream));
         else
-            s = inv ? jfft::launch_pass_t<double, true>(N, a, grid, block, p->stream)
-                    : jfft::launch_pass_t<double, false>(N, a, grid, block, p->stream);
+            s = inv ? (yz ? jfft::launch_pass_t<double, true, true>(N, a, grid, block, p->stream)
+                          : jfft::launch_pass_t<double, true, false>(N, a, grid, block, p->stream))
+                    : (yz ? jfft::launch_pass_t<double, false, true>(N, a, grid, block, p->stream)
+                          : jfft::launch_pass_t<double, false, false>(N, a, grid, block, p->stream));
         if (s != JAC_OK) return plan_from_thread(p, s);
     }
     return JAC_OK;

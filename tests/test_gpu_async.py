@@ -132,3 +132,31 @@ def test_two_contexts_in_turn(prec):
         assert g == wg, k
     op, og = oracle_ref(fs[0], n, prec)
     assert rel_p(got[0][1], op) <= TOL[prec] and rel_g(got[0][2], og) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16", "f64"])
+@pytest.mark.parametrize("dims,n", [((33, 33, 65), 7), ((131, 10, 6), 3)])
+def test_fp32_host_copies_equal_fp64_copies_of_the_same_numbers(prec, dims, n):
+    """jac_upload_f32_async of FP32 host arrays stores exactly what
+    jac_upload_async stores for the same numbers held in FP64, so the state
+    and residual are bitwise equal; jac_download_f32_async gives the state
+    rounded to FP32 (exact for FP32 storage).  The result also matches the
+    oracle on that problem."""
+    import torch
+    from paper_2002_12115_gb300 import Jacobi
+    I, J, K = dims
+    f64 = ji.himeno_fields(I, J, K, seed=320 + I)
+    f = {k: v.astype(np.float32).astype(np.float64) for k, v in f64.items()}     # FP32 numbers
+    want_p, want_g = gpu_run(f, n, prec)
+    h32 = {k: torch.from_numpy(v.astype(np.float32)).pin_memory().numpy() for k, v in f.items()}
+    out32 = torch.empty((K, J, I), dtype=torch.float32, pin_memory=True).numpy()
+    res = pinned((1,))
+    with Jacobi(I, J, K, prec, OMEGA) as jac:
+        jac.upload_f32_async(h32)
+        jac.sweep(n)
+        jac.download_f32_async(out32, res)
+        jac.sync()
+    assert res[0] == want_g
+    assert np.array_equal(out32, want_p.astype(np.float32))
+    op, og = oracle_ref(f, n, prec)
+    assert rel_p(out32.astype(np.float64), op) <= max(TOL[prec], 1e-7) and rel_g(res[0], og) <= TOL[prec]

@@ -27,7 +27,7 @@ def plan(I, J, K, prec, **kw):
     # FP64: rounds x (kdepth + 3), or balanced ranges where those cost less
     ((129, 129, 257), "f64", (64, 8, KDEPTH_BALANCED)),
     ((513, 513, 1025), "f64", (64, 8, KDEPTH_BALANCED)),
-    ((33, 33, 65), "f64", (32, 16, 2)),
+    ((33, 33, 65), "f64", (32, 16, 1)),
     ((65, 65, 129), "f64", (64, 8, 7)),
 ])
 def test_default_plans(dims, prec, want):
