@@ -90,10 +90,11 @@ typedef struct jac_fields_f32 {
 
 /* Storage pitch (elements) of every array of an I-wide grid: I rounded up to
  * a multiple of 8, so that each row starts on a 16-byte boundary in every
- * element type (the TMA stride rule) and vector loads stay aligned. */
+ * element type (the TMA stride rule) and vector loads stay aligned.  No
+ * paper counterpart (device layout). */
 int jac_pitch(int I);
 
-/* Library version string (static storage). */
+/* Library version string (static storage).  No paper counterpart. */
 const char *jac_version(void);
 
 /* =====================================================================
@@ -149,7 +150,9 @@ typedef struct jac_plan {
                      an even number of passes. */
 } jac_plan;
 
-/* The plan a sweep of this grid would run with on a device of sm_count SMs
+/* Paper: launch parameters chosen by rule where the rule is known and by
+ * measurement otherwise (Section 4).
+ * The plan a sweep of this grid would run with on a device of sm_count SMs
  * (one CTA per SM; sm_count <= 0: the current device's count): the zero
  * fields of *plan (NULL: all zero) filled in by the rules above.  Only the
  * dimensions and the precision of *g are read; no device memory is touched,
@@ -157,7 +160,9 @@ typedef struct jac_plan {
  * dimensions, precision or plan entries, or a shape the kernels lack. */
 jac_status jac_resolve_plan(const jac_grid *g, const jac_plan *plan, int sm_count, jac_plan *out);
 
-/* Bytes of device workspace jac_sweep_dev needs for this grid and plan. */
+/* Bytes of device workspace jac_sweep_dev needs for this grid and plan
+ * (host only).  No paper counterpart (the caller-owned scratch of the
+ * stateless form). */
 jac_status jac_sweep_workspace_size(const jac_grid *g, const jac_plan *plan, size_t *bytes);
 
 /* n_iter sweeps of grid g on the given stream (a cudaStream_t, NULL for the
@@ -176,16 +181,20 @@ jac_status jac_sweep_dev(const jac_grid *g, const jac_plan *plan, int n_iter,
                          void *stream);
 
 /* Reads the device error word kept in a workspace (synchronises the
- * stream): JAC_OK, or JAC_ETIMEOUT if a bounded wait gave up; clears it. */
+ * stream): JAC_OK, or JAC_ETIMEOUT if a bounded wait gave up; clears it.
+ * Paper: the offload search gives up a measurement after a time limit
+ * (Section 5.1.2); the kernels give up their device waits likewise. */
 jac_status jac_workspace_check(void *workspace, void *stream);
 
 /* Convert one dense FP64 device array (I*J*K doubles) into storage layout of
  * element type `prec` uses for array `which` (JAC_P .. JAC_BND), on stream.
- * Padding columns are set to zero. */
+ * Padding columns are set to zero.  Paper: the device side of the hoisted
+ * copy-in (Sections 3.2-3.3). */
 jac_status jac_pack_dev(int I, int J, int K, jac_prec prec, int which,
                         const double *d_src, void *d_dst, void *stream);
 
-/* Convert one storage-layout array back to dense FP64 (device memory). */
+/* Convert one storage-layout array back to dense FP64 (device memory).
+ * Paper: the device side of the hoisted copy-out (Section 3.3). */
 jac_status jac_unpack_dev(int I, int J, int K, jac_prec prec, int which,
                           const void *d_src, double *d_dst, void *stream);
 
@@ -298,23 +307,29 @@ jac_status jac_create_borrowed(jac_ctx **out, const jac_grid *fields, void *stre
  * jac_create_borrowed, JAC_ECUDA. */
 jac_status jac_set_workspace(jac_ctx *ctx, void *workspace, size_t ws_bytes, const jac_ws_spec *spec);
 
-/* Free everything the context owns (synchronises its stream).  NULL is ok. */
+/* Free everything the context owns (synchronises its stream); a borrowed
+ * context's memory stays the caller's.  NULL is ok.  No paper counterpart. */
 jac_status jac_destroy(jac_ctx *ctx);
 
-/* Message of the last failed call on this context ("" if none). */
+/* Message of the last failed call on this context ("" if none; NULL: the
+ * calling thread's last message).  No paper counterpart. */
 const char *jac_last_error(const jac_ctx *ctx);
 
-/* Set the launch plan of later sweeps ({0,0} = defaults). */
+/* Set the launch plan of later sweeps ({0,0} = defaults).  Paper: launch
+ * parameters chosen by rule or by measurement (Section 4, the search by
+ * measurement that the autotuner applies to launch plans). */
 jac_status jac_set_plan(jac_ctx *ctx, const jac_plan *plan);
 
-/* The hoisted copy-in: all thirteen host FP64 arrays, rounded to the storage
+/* The hoisted copy-in (Sections 3.2-3.3: all variables copied once, before
+ * all GPU work): all thirteen host FP64 arrays, rounded to the storage
  * precision on the device; p0 goes to both state buffers.  Resets the sweep
  * count and the residual.  Returns after the copies are enqueued (host
  * arrays may be reused once the call returns: pageable sources are copied
  * synchronously, and the call synchronises before returning). */
 jac_status jac_upload(jac_ctx *ctx, const jac_fields *host);
 
-/* Same as jac_upload without waiting: the thirteen host-to-device copies go
+/* Same as jac_upload without waiting (Sections 3.2-3.3, with the copies
+ * overlapping other work): the thirteen host-to-device copies go
  * into thirteen device staging arrays (13*I*J*K doubles, allocated by the
  * first call and owned by the context), and the rounding kernels follow them
  * on the stream, so the copies can run on the copy engine while another
@@ -337,25 +352,31 @@ jac_status jac_upload_async(jac_ctx *ctx, const jac_fields *host);
 jac_status jac_upload_f32_async(jac_ctx *ctx, const jac_fields_f32 *host);
 
 /* Same as jac_upload with the thirteen arrays in device memory (dense FP64);
- * asynchronous. */
+ * asynchronous.  Paper: data already present on the device (Section 3.3). */
 jac_status jac_upload_dev(jac_ctx *ctx, const jac_fields *dev);
 
 /* n_iter sweeps, asynchronous; the residual of the last one is kept on the
- * device.  JAC_ESTATE before the first upload. */
+ * device.  JAC_ESTATE before the first upload.  Paper: the Himeno Jacobi
+ * loop (Section 5.1.1) on arrays present on the device (Section 3.3). */
 jac_status jac_sweep(jac_ctx *ctx, int n_iter);
 
 /* Residual of the last sweep (synchronises).  JAC_ESTATE if no sweep ran
- * since the last upload; JAC_ETIMEOUT if a device wait gave up. */
+ * since the last upload; JAC_ETIMEOUT if a device wait gave up.  Paper: the
+ * Himeno residual (Section 5.1.1), the value the result check compares
+ * between CPU and GPU runs (Section 4). */
 jac_status jac_residual(jac_ctx *ctx, double *out);
 
-/* The hoisted copy-out: current state as dense FP64 into host memory
- * (I*J*K doubles; synchronises). */
+/* The hoisted copy-out (Section 3.3: copied back once, after all GPU
+ * work): current state as dense FP64 into host memory (I*J*K doubles;
+ * synchronises). */
 jac_status jac_download(jac_ctx *ctx, double *p_host);
 
-/* Current state as dense FP64 into device memory (asynchronous). */
+/* Current state as dense FP64 into device memory (asynchronous).  Paper:
+ * Section 3.3 (the result stays on the device for later GPU work). */
 jac_status jac_download_dev(jac_ctx *ctx, double *p_dev);
 
-/* jac_download and jac_residual without waiting: enqueues the copy of the
+/* jac_download and jac_residual without waiting (Section 3.3, overlapped
+ * with other work): enqueues the copy of the
  * current state (I*J*K doubles) to p_host and, if res_host is not NULL, of
  * the residual of the last sweep to *res_host.  Both are valid once the
  * stream has passed them (jac_sync); pinned destinations give asynchronous
@@ -369,7 +390,8 @@ jac_status jac_download_async(jac_ctx *ctx, double *p_host, double *res_host);
  * FP64.  Valid after jac_sync.  Errors: as jac_download_async. */
 jac_status jac_download_f32_async(jac_ctx *ctx, float *p_host, double *res_host);
 
-/* Wait for the context's stream and check the sweep workspace's error word:
+/* Paper: Section 5.1.2 (time-limited waits, as for jac_workspace_check).
+ * Wait for the context's stream and check the sweep workspace's error word:
  * JAC_ETIMEOUT if a bounded device wait of an earlier sweep gave up (the
  * word is cleared), JAC_ECUDA on a CUDA error. */
 jac_status jac_sync(jac_ctx *ctx);
@@ -388,11 +410,12 @@ jac_status jac_sync(jac_ctx *ctx);
  * or hangs: every wait is bounded.  Errors: JAC_EINVAL. */
 jac_status jac_inject_stall(jac_ctx *ctx, unsigned long long wait_ns);
 
-/* Sweeps completed since the last upload. */
+/* Sweeps completed since the last upload.  No paper counterpart. */
 jac_status jac_sweep_count(const jac_ctx *ctx, long long *out);
 
 /* The context's grid descriptor (current state in p[count % 2] order is
- * handled by the context; g->p[0] is the current state after this call). */
+ * handled by the context; g->p[0] is the current state after this call).
+ * No paper counterpart. */
 jac_status jac_get_grid(const jac_ctx *ctx, jac_grid *g);
 
 /* ---------------------------------------------------------------------
@@ -425,17 +448,19 @@ jac_status jac_adjoint_step_dev(const jac_grid *g, const void *p_t, const void *
                                 double *g_wrk1, double *g_a3, double *const *g_coef, int kdepth,
                                 void *workspace, size_t ws_bytes, void *stream);
 
-/* Start a checkpoint tape: the next sweeps (at most max_sweeps, across any
+/* No paper counterpart (differentiation addition).
+ * Start a checkpoint tape: the next sweeps (at most max_sweeps, across any
  * number of jac_sweep calls) are recorded by saving the state at the start
  * of every C-sweep segment.  Allocates ceil(max_sweeps/C) + C + 1 state
  * arrays.  A new upload or jac_tape_end discards the tape. */
 jac_status jac_tape_begin(jac_ctx *ctx, int C, int max_sweeps);
 jac_status jac_tape_end(jac_ctx *ctx);
 
-/* Sweeps recorded on the tape so far. */
+/* Sweeps recorded on the tape so far.  No paper counterpart. */
 jac_status jac_tape_count(const jac_ctx *ctx, int *out);
 
-/* Reverse pass over the taped sweeps for a terminal adjoint lambda_T
+/* No paper counterpart (differentiation addition).
+ * Reverse pass over the taped sweeps for a terminal adjoint lambda_T
  * (dense FP64, device; e.g. p_T - target for L = 1/2 |p_T - target|^2).
  * Each segment is recomputed from its checkpoint into C state buffers, then
  * swept backwards.  Outputs (dense FP64, device, overwritten): g_wrk1,
@@ -453,7 +478,8 @@ jac_status jac_sweep_adjoint(jac_ctx *ctx, const double *lambda_T, double *g_wrk
  * --------------------------------------------------------------------- */
 typedef struct jac_batch jac_batch;
 
-/* n grids, dims[3g..3g+2] = I, J, K of grid g (each >= 3).  Allocates every
+/* No paper counterpart (see above).
+ * n grids, dims[3g..3g+2] = I, J, K of grid g (each >= 3).  Allocates every
  * grid's storage (cudaMalloc), a staging array of the largest grid and n
  * residuals.  stream: the cudaStream_t of every call. */
 jac_status jac_batch_create(jac_batch **out, int n, const int *dims, jac_prec prec, double omega,
@@ -462,40 +488,47 @@ jac_status jac_batch_destroy(jac_batch *b);
 const char *jac_batch_last_error(const jac_batch *b);
 
 /* Hoisted copy-in of grid g (host or device dense FP64 arrays, as for
- * jac_upload / jac_upload_dev). */
+ * jac_upload / jac_upload_dev; Sections 3.2-3.3). */
 jac_status jac_batch_upload(jac_batch *b, int g, const jac_fields *host);
 jac_status jac_batch_upload_dev(jac_batch *b, int g, const jac_fields *dev);
 
-/* Launch plan: `warps` consumer warps per CTA for the whole launch (4 or 8;
+/* Paper: the plan the autotuner finds by measurement (Section 4, the GA's
+ * search by measured run time, Section 5.1.2 for its settings).
+ * Launch plan: `warps` consumer warps per CTA for the whole launch (4 or 8;
  * 16 with BF16 coefficients; 0 = 8) and per grid a tile width tile_i[g] (a
  * power of two in [16, 128] for FP32/BF16, [16, 64] for FP64; 0 = the width
  * with the best lane use) and k-block depth kdepth[g] (0 = default).  NULL
  * arrays mean all defaults.  The next sweep rebuilds the device tables. */
 jac_status jac_batch_set_plan(jac_batch *b, int warps, const int *tile_i, const int *kdepth);
 
-/* The plan grid g will run with (after defaults). */
+/* The plan grid g will run with (after defaults).  No paper counterpart. */
 jac_status jac_batch_grid_plan(const jac_batch *b, int g, jac_plan *out);
 
-/* n_iter sweeps of every grid in one persistent launch (captured in a CUDA
+/* Paper: the Himeno loop (Section 5.1.1) for many grids at once.
+ * n_iter sweeps of every grid in one persistent launch (captured in a CUDA
  * graph on first use for this n_iter and buffer parity, then replayed).
  * If res_host is not NULL it receives the n residuals of the last sweep.
  * Synchronises.  JAC_ETIMEOUT if a bounded device wait gave up. */
 jac_status jac_batch_sweep(jac_batch *b, int n_iter, double *res_host);
 
-/* The same sweeps as a loop of per-grid launches, for comparison: one
+/* No paper counterpart (measurement contrast).
+ * The same sweeps as a loop of per-grid launches, for comparison: one
  * cooperative launch of n_iter sweeps per grid (per_sweep = 0), or one
  * launch per sweep per grid (per_sweep != 0). */
 jac_status jac_batch_sweep_loop(jac_batch *b, int n_iter, int per_sweep, double *res_host);
 
-/* Current state of grid g as dense FP64 (host: synchronises; device: async). */
+/* Current state of grid g as dense FP64 (host: synchronises; device:
+ * async).  Paper: the hoisted copy-out (Section 3.3). */
 jac_status jac_batch_download(jac_batch *b, int g, double *p_host);
 jac_status jac_batch_download_dev(jac_batch *b, int g, double *p_dev);
 
 /* Work items and CTAs of the current plan (0 before the first sweep), the
- * warp count and the sweeps run so far. */
+ * warp count and the sweeps run so far.  No paper counterpart. */
 jac_status jac_batch_info(const jac_batch *b, int *n_items, int *n_ctas, int *warps, long long *sweeps);
 
-/* The contrast to hoisting, for measurement only: for each of n_iter
+/* Paper: what transfer hoisting avoids (Section 3.2: copies inside the
+ * loop nest instead of outside it).
+ * The contrast to hoisting, for measurement only: for each of n_iter
  * sweeps, copy all thirteen host arrays in (the current host state as p),
  * run one sweep, copy p back out to p_host.  On entry p_host holds p0; on
  * return it holds p_n, and the context's residual is that of sweep n. */
