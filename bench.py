@@ -64,6 +64,7 @@ WORKLOADS = {
     "fft": dict(n=(512, 512, 512), prec="c32", alpha=1e-5),
     "fft-c64": dict(n=(512, 512, 512), prec="c64", alpha=1e-5),
     "fft-profile": dict(n=(256, 256, 256), prec="c32", alpha=1e-5),
+    "fft-profile-c64": dict(n=(256, 256, 256), prec="c64", alpha=1e-5),
     "medium-bf16": dict(I=257, J=257, K=513, sweeps=100, prec="bf16"),
     "batch": dict(n_grids=512, sweeps=100, prec="f32"),
     "batch-f64": dict(n_grids=512, sweeps=100, prec="f64"),
@@ -815,7 +816,7 @@ def bench_fft(args, w, stream, steps=None, warmup=None, e2e=True, parity=True):
                     "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                                  "frac": achieved / peak, "peak_kind": kind,
                                  "bytes_per_point": FFT_BYTES_PER_POINT[prec],
-                                 "kernel": "k_fft_pass (3 launches per step)"}})
+                                 "kernel": "k_fft_pass (3 passes per step, plus the factor and energy kernels)"}})
         if e2e:
             host_u0 = torch.empty(u0.shape, dtype=cdt, pin_memory=True)
             host_u0.copy_(u0)
@@ -970,7 +971,7 @@ def run_native(args, w, wname):
                                 "l2": f"inputs larger than L2 ({n1 * n2 * n3 * (8 if w['prec'] == 'c32' else 16) / 1e6:.0f}"
                                       " MB per array); no flush"},
                      "roofline": dict(r["roofline"], traffic=None), "e2e": r.get("e2e"), "parity": r.get("parity"),
-                     "gpu_launches": 3 * args.steps, "fft": r})
+                     "gpu_launches": 5 * args.steps, "fft": r})
     if wname.startswith("adjoint"):
         r = bench_adjoint(args, w, stream, steps=args.steps)
         ms = max_over_ranks(r["ms_per_pass"], args.dist)

@@ -20,8 +20,8 @@
 //   * the spectral step multiplies the data by exp(-4 pi^2 alpha t |kbar|^2)
 //     as the first pass loads it (a per-CTA table of the factor along the
 //     axis times one factor per line), and the last pass scales by 1/N as it
-//     stores and sums |u|^2 per CTA in FP64; the last CTA to finish adds the
-//     per-CTA sums in CTA order, so the energy is bitwise reproducible.
+//     stores and sums |u|^2 per CTA in FP64; a one-CTA kernel then adds the
+//     per-CTA sums in a fixed order, so the energy is bitwise reproducible.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -183,8 +183,7 @@ struct PassArgs {
     const void *fa;          // factor tables exp(c kbar^2) (element type T): this pass's axis,
     const void *fb;          // and the line's other two axes (for the pass along x: y, then z)
     const void *fc;
-    double *partials;        // per-CTA sums of |u|^2 (energy != NULL)
-    unsigned *counter;       // CTAs done (last one reduces and resets it)
+    double *partials;        // per-CTA sums of |u|^2 (written when energy != NULL)
     double *energy;
 };
 
@@ -346,8 +345,8 @@ __global__ void __launch_bounds__(512) k_fft_pass(const PassArgs a)
     if (!want_energy) return;
 
     // energy: block sum (warp shuffles when the block is whole warps, else
-    // one thread in thread order), then the last CTA adds the per-CTA sums
-    // in CTA order
+    // one thread in thread order) into this CTA's partial; k_fft_energy adds
+    // the partials in CTA order after the pass
     int nred = blockDim.x;
     if ((blockDim.x & 31) == 0) {
 #pragma unroll
@@ -358,42 +357,38 @@ __global__ void __launch_bounds__(512) k_fft_pass(const PassArgs a)
         red[threadIdx.x] = esum;
     }
     __syncthreads();
-    __shared__ int s_last;
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int i = 0; i < nred; ++i) s += red[i];
         a.partials[blockIdx.x] = s;
-        __threadfence();
-        s_last = atomicAdd(a.counter, 1u) == gridDim.x - 1;
     }
-    __syncthreads();
-    if (s_last) {
-        // every thread sums the partials b = tid, tid + blockDim, ... in
-        // order (Neumaier), then thread 0 adds those sums in thread order:
-        // a fixed order for a given launch shape
-        __threadfence();
-        double s = 0.0, comp = 0.0;
+}
+
+// Sum of the n per-CTA energy partials of the last pass, in a fixed order:
+// thread t adds the partials t, t + blockDim, ... (Neumaier), then thread 0
+// adds the threads' sums in thread order.  One CTA of 512 threads.
+__global__ void __launch_bounds__(512) k_fft_energy(const double *__restrict__ partials, int n, double *energy)
+{
+    __shared__ double red[512];
+    double s = 0.0, comp = 0.0;
 #pragma unroll 4
-        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
-            const double x = __ldcg(&a.partials[b]);
-            const double tsum = s + x;
-            comp += fabs(s) >= fabs(x) ? (s - tsum) + x : (x - tsum) + s;
-            s = tsum;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+        const double x = partials[b];
+        const double tsum = s + x;
+        comp += fabs(s) >= fabs(x) ? (s - tsum) + x : (x - tsum) + s;
+        s = tsum;
+    }
+    red[threadIdx.x] = s + comp;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double e = 0.0, ec = 0.0;
+        for (unsigned i = 0; i < blockDim.x; ++i) {
+            const double x = red[i];
+            const double tsum = e + x;
+            ec += fabs(e) >= fabs(x) ? (e - tsum) + x : (x - tsum) + e;
+            e = tsum;
         }
-        red[threadIdx.x] = s + comp;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double e = 0.0, ec = 0.0;
-            for (unsigned i = 0; i < blockDim.x; ++i) {
-                const double x = red[i];
-                const double tsum = e + x;
-                ec += fabs(e) >= fabs(x) ? (e - tsum) + x : (x - tsum) + e;
-                e = tsum;
-            }
-            *a.energy = e + ec;
-            *a.counter = 0u;
-            __threadfence();
-        }
+        *energy = e + ec;
     }
 }
 
@@ -451,7 +446,7 @@ struct Layout {
 Layout layout(const int n[3], jfft_prec prec)
 {
     Layout L;
-    size_t off = 256;                     // header: the CTA counter
+    size_t off = 256;                     // header (reserved)
     for (int a = 0; a < 3; ++a) {
         L.tw[a] = off;
         off += round256((size_t)n[a] * elem_bytes(prec));
@@ -605,7 +600,6 @@ jac_status run3(jfft_plan *p, const void *in, void *out, bool inv, double scale,
         if (axis == 2 && energy) {
             a.energy = energy;
             a.partials = reinterpret_cast<double *>(p->ws + p->L.partials);
-            a.counter = reinterpret_cast<unsigned *>(p->ws);
         }
         const unsigned grid = (unsigned)jfft::ctas_of_pass(axis, p->n, a.W);
         const unsigned block = (unsigned)jfft::threads_of_pass(N, a.W, p->prec, axis != 0);
@@ -622,6 +616,12 @@ jac_status run3(jfft_plan *p, const void *in, void *out, bool inv, double scale,
                     : (yz ? jfft::launch_pass_t<double, false, true>(N, a, grid, block, p->stream)
                           : jfft::launch_pass_t<double, false, false>(N, a, grid, block, p->stream));
         if (s != JAC_OK) return plan_from_thread(p, s);
+        if (axis == 2 && energy) {
+            jfft::k_fft_energy<<<1, 512, 0, p->stream>>>(reinterpret_cast<double *>(p->ws + p->L.partials), (int)grid,
+                                                         energy);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return plan_fail(p, JAC_ECUDA, std::string("energy launch: ") + cudaGetErrorString(e));
+        }
     }
     return JAC_OK;
 }
