@@ -947,7 +947,7 @@ def run_native(args, w, wname):
     if wname == "tuners":
         r = bench_tuners(stream, sweeps=w["sweeps"])
         return emit({"metric": METRIC + " (512-grid batch under each launch-plan search)",
-                     "value": max(v["value"] for v in r.values()), "unit": UNIT, "n_gpus": world,
+                     "value": max(v["value"] for k, v in r.items() if "value" in v), "unit": UNIT, "n_gpus": world,
                      "higher_is_better": True, "dtype": "f32", "data": "synthetic",
                      "config": {"workload": "512 grids, dims drawn from {17,33,49,65,97,129}, f32, 100 sweeps; "
                                             "plans searched from scratch"},
