@@ -141,14 +141,15 @@ struct Radix {
 
 // Elements of a line each thread holds.  The pass along x keeps the
 // largest radix (more lanes along each row); the passes along y and z take
-// up to 16, so that fewer threads serve a line and a CTA of 256 threads
-// covers more consecutive x.
+// up to 32 (FP32) or 16 (FP64) so that fewer threads serve a line and a CTA
+// of at most 512 threads covers 256 bytes of consecutive x.
 template <typename T, int N, bool YZ>
 __host__ __device__ constexpr int elems_per_thread()
 {
     constexpr int rmax = Radix<N>::RMAX;
+    constexpr int cap = sizeof(T) == 4 ? 32 : 16;
     constexpr int want = N / 16 > rmax ? N / 16 : rmax;
-    return YZ ? (want < 16 ? want : 16) : rmax;
+    return YZ ? (want < cap ? want : cap) : rmax;
 }
 
 // Shared-memory index of element e of a line: one pad element after every
@@ -176,8 +177,7 @@ struct PassArgs {
     const void *tw;          // W_N^m, m = 0 .. N-1, of this axis (forward sign)
     int n1, n2, n3;
     int axis;                // 0: x, 1: y, 2: z
-    int W;                   // lines per tile
-    int ntiles;              // tiles of the pass (CTA b takes b, b + G, ...)
+    int W;                   // lines per CTA
     double scale;            // applied by the last stage (1 or 1/N)
     int factor;              // multiply by the spectral factor on load (first pass of a step)
     const void *fa;          // factor tables exp(c kbar^2) (element type T): this pass's axis,
@@ -205,53 +205,33 @@ __global__ void k_fft_factors(double c, int n1, int n2, int n3, T *f1, T *f2, T 
     else if (i < n1 + n2 + n3) f3[i - n1 - n2] = (T)exp(c * kbar2(i - n1 - n2, n3));
 }
 
-// The inputs of the first stage of this thread's line, from global memory
-// (issued ahead of use: the loads of the next tile stay in flight while the
-// current tile's later stages run).
-template <typename T, int N, int R, int RMAX>
-__device__ __forceinline__ void gather_first(C2<T> (&v)[RMAX], const C2<T> *gin, long long lb, long long es, int t)
-{
-    constexpr int TT = N / RMAX;
-    constexpr int BPT = RMAX / R;
-#pragma unroll
-    for (int q = 0; q < BPT; ++q)
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[q * R + r] = gin[lb + (long long)(t + q * TT + r * (N / R)) * es];
-}
-
-// The spectral factor on the first stage's inputs: element e of the line
-// times fe[e] * fl (the factor along the pass's axis and the line's).
-template <typename T, int N, int R, int RMAX>
-__device__ __forceinline__ void apply_factor(C2<T> (&v)[RMAX], int t, const T *fe, T fl)
-{
-    constexpr int TT = N / RMAX;
-    constexpr int BPT = RMAX / R;
-#pragma unroll
-    for (int q = 0; q < BPT; ++q)
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const T f = fe[t + q * TT + r * (N / R)] * fl;
-            v[q * R + r].x *= f;
-            v[q * R + r].y *= f;
-        }
-}
-
-// One Stockham stage for the BPT = RMAX / R butterflies of this thread.  The
-// first stage's inputs are already in v (gather_first).
+// One Stockham stage for the BPT = RMAX / R butterflies of this thread.
 template <typename T, int N, int R, int RMAX, int NS, bool INV, bool FIRST, bool LAST>
-__device__ __forceinline__ void stage(C2<T> (&v)[RMAX], C2<T> *tile, const C2<T> *tw, C2<T> *gout, long long lb,
-                                      long long es, int w, int t, T scale, double &esum, bool want_energy)
+__device__ __forceinline__ void stage(C2<T> (&v)[RMAX], C2<T> *tile, const C2<T> *tw, const C2<T> *gin, C2<T> *gout,
+                                      long long lb, long long es, int w, int t, const T *fe, T fl, T scale,
+                                      bool factor, double &esum, bool want_energy)
 {
     constexpr int TT = N / RMAX;       // threads per line
     constexpr int BPT = RMAX / R;      // butterflies per thread
     constexpr int RS = row_stride<T, N>();
     C2<T> *row = tile + w * RS;
-    if constexpr (!FIRST) {
 #pragma unroll
-        for (int q = 0; q < BPT; ++q) {
-            const int j = t + q * TT;
+    for (int q = 0; q < BPT; ++q) {
+        const int j = t + q * TT;
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[q * R + r] = row[pad_idx<T>(j + r * (N / R))];
+        for (int r = 0; r < R; ++r) {
+            const int e = j + r * (N / R);
+            if constexpr (FIRST) {
+                C2<T> x = gin[lb + (long long)e * es];
+                if (factor) {
+                    const T f = fe[e] * fl;
+                    x.x *= f;
+                    x.y *= f;
+                }
+                v[q * R + r] = x;
+            } else {
+                v[q * R + r] = row[pad_idx<T>(e)];
+            }
         }
     }
     if constexpr (!FIRST && !LAST) __syncthreads();   // every read of the tile before any write
@@ -288,50 +268,43 @@ __device__ __forceinline__ void stage(C2<T> (&v)[RMAX], C2<T> *tile, const C2<T>
     if constexpr (!LAST) __syncthreads();
 }
 
-// The first element and element stride of this thread's line in tile `tile`
-// of a pass, and the line's indices on the other two axes (ia: y for the
-// pass along x, else x; ib: z for the passes along x and y, else y).
-__device__ __forceinline__ void line_of(const PassArgs &a, int tile, int w, long long &lb, long long &es, int &ia,
-                                        int &ib)
-{
-    const long long n1 = a.n1, n2 = a.n2;
-    if (a.axis == 0) {
-        const long long row = (long long)tile * a.W + w;         // row = z * n2 + y
-        lb = row * n1;
-        es = 1;
-        ia = (int)(row % n2);
-        ib = (int)(row / n2);
-    } else {
-        const int xt = tile % (a.n1 / a.W);
-        const int o = tile / (a.n1 / a.W);                       // z (y pass) or y (z pass)
-        const int x = xt * a.W + w;
-        ia = x;
-        ib = o;
-        lb = a.axis == 1 ? (long long)o * n1 * n2 + x : (long long)o * n1 + x;
-        es = a.axis == 1 ? n1 : n1 * n2;
-    }
-}
-
-// A pass over `ntiles` tiles of W lines; CTA b takes the tiles b, b + G,
-// b + 2G, ... and loads each next tile's first-stage inputs into registers
-// while it finishes the current one.
 template <typename T, int N, bool INV, bool YZ>
-__global__ void __launch_bounds__(256) k_fft_pass(const PassArgs a)
+__global__ void __launch_bounds__(512) k_fft_pass(const PassArgs a)
 {
     using RX = Radix<N>;
     constexpr int RMAX = elems_per_thread<T, N, YZ>();   // elements per thread
     constexpr int TT = N / RMAX;
+    constexpr int RS = row_stride<T, N>();
     extern __shared__ __align__(16) unsigned char jfft_smem[];
     const int W = a.W;
     C2<T> *tile = reinterpret_cast<C2<T> *>(jfft_smem);
-    C2<T> *tw = tile + (RX::R2 > 1 ? W * row_stride<T, N>() : 0);
+    C2<T> *tw = tile + (RX::R2 > 1 ? W * RS : 0);
     T *fe = reinterpret_cast<T *>(tw + N);
-    __shared__ double red[256];
+    T *fl = fe + N;
+    __shared__ double red[512];
 
-    // this thread's line within a tile and its position in the line
+    // this thread's line and position in it
     int w, t;
     if (a.axis == 0) { t = threadIdx.x % TT; w = threadIdx.x / TT; }
     else { w = threadIdx.x % W; t = threadIdx.x / W; }
+    const long long n1 = a.n1, n2 = a.n2;
+    long long lb, es;              // first element of the line, element stride
+    int ia, ib, na, nb;            // the line's indices on the other two axes, and their extents
+    if (a.axis == 0) {
+        const long long row = (long long)blockIdx.x * W + w;     // row = z * n2 + y
+        lb = row * n1;
+        es = 1;
+        ia = (int)(row % n2); na = a.n2;
+        ib = (int)(row / n2); nb = a.n3;
+    } else {
+        const int xt = blockIdx.x % (a.n1 / W);
+        const int o = blockIdx.x / (a.n1 / W);                   // z (y pass) or y (z pass)
+        const int x = xt * W + w;
+        ia = x; na = a.n1;
+        ib = o; nb = a.axis == 1 ? a.n3 : a.n2;
+        lb = a.axis == 1 ? (long long)o * n1 * n2 + x : (long long)o * n1 + x;
+        es = a.axis == 1 ? n1 : n1 * n2;
+    }
 
     // twiddles (and the spectral factor along this axis) into shared memory
     const C2<T> *gtw = static_cast<const C2<T> *>(a.tw);
@@ -340,53 +313,34 @@ __global__ void __launch_bounds__(256) k_fft_pass(const PassArgs a)
         if constexpr (RX::R2 > 1) tw[m] = gtw[m];
         if (a.factor) fe[m] = gfa[m];
     }
+    if (a.factor && t == 0) fl[w] = static_cast<const T *>(a.fb)[ia] * static_cast<const T *>(a.fc)[ib];
+    (void)na;
+    (void)nb;
     __syncthreads();
 
     const C2<T> *gin = static_cast<const C2<T> *>(a.in);
     C2<T> *gout = static_cast<C2<T> *>(a.out);
-    const T *gfb = static_cast<const T *>(a.fb);
-    const T *gfc = static_cast<const T *>(a.fc);
     const bool want_energy = a.energy != nullptr;
     const T scale = (T)a.scale;
+    const T flw = a.factor ? fl[w] : (T)1;
     double esum = 0.0;
+    C2<T> v[RMAX];
     constexpr int R1 = RX::R1, R2 = RX::R2, R3 = RX::R3;
-
-    int tile_id = blockIdx.x;
-    long long lb, es;
-    int ia, ib;
-    line_of(a, tile_id, w, lb, es, ia, ib);
-    C2<T> v[RMAX], vn[RMAX];
-    gather_first<T, N, R1, RMAX>(v, gin, lb, es, t);
-    while (true) {
-        const int next = tile_id + (int)gridDim.x;
-        long long lbn = 0, esn = 0;
-        int ian = 0, ibn = 0;
-        if (next < a.ntiles) line_of(a, next, w, lbn, esn, ian, ibn);
-        if (a.factor) apply_factor<T, N, R1, RMAX>(v, t, fe, gfb[ia] * gfc[ib]);
-        if constexpr (R2 == 1) {
-            if (next < a.ntiles) gather_first<T, N, R1, RMAX>(vn, gin, lbn, esn, t);
-            stage<T, N, R1, RMAX, 1, INV, true, true>(v, tile, tw, gout, lb, es, w, t, scale, esum, want_energy);
-        } else if constexpr (R3 == 1) {
-            stage<T, N, R1, RMAX, 1, INV, true, false>(v, tile, tw, gout, lb, es, w, t, scale, esum, want_energy);
-            if (next < a.ntiles) gather_first<T, N, R1, RMAX>(vn, gin, lbn, esn, t);
-            stage<T, N, R2, RMAX, R1, INV, false, true>(v, tile, tw, gout, lb, es, w, t, scale, esum, want_energy);
-        } else {
-            stage<T, N, R1, RMAX, 1, INV, true, false>(v, tile, tw, gout, lb, es, w, t, scale, esum, want_energy);
-            if (next < a.ntiles) gather_first<T, N, R1, RMAX>(vn, gin, lbn, esn, t);
-            stage<T, N, R2, RMAX, R1, INV, false, false>(v, tile, tw, gout, lb, es, w, t, scale, esum,
-                                                         want_energy);
-            stage<T, N, R3, RMAX, R1 * R2, INV, false, true>(v, tile, tw, gout, lb, es, w, t, scale, esum,
-                                                             want_energy);
-        }
-        if (next >= a.ntiles) break;
-        if constexpr (R2 > 1) __syncthreads();   // the last stage's tile reads before the next tile's writes
-#pragma unroll
-        for (int k = 0; k < RMAX; ++k) v[k] = vn[k];
-        tile_id = next;
-        lb = lbn;
-        es = esn;
-        ia = ian;
-        ib = ibn;
+    if constexpr (R2 == 1) {
+        stage<T, N, R1, RMAX, 1, INV, true, true>(v, tile, tw, gin, gout, lb, es, w, t, fe, flw, scale,
+                                                  a.factor, esum, want_energy);
+    } else if constexpr (R3 == 1) {
+        stage<T, N, R1, RMAX, 1, INV, true, false>(v, tile, tw, gin, gout, lb, es, w, t, fe, flw, scale,
+                                                   a.factor, esum, want_energy);
+        stage<T, N, R2, RMAX, R1, INV, false, true>(v, tile, tw, gin, gout, lb, es, w, t, fe, flw, scale,
+                                                    a.factor, esum, want_energy);
+    } else {
+        stage<T, N, R1, RMAX, 1, INV, true, false>(v, tile, tw, gin, gout, lb, es, w, t, fe, flw, scale,
+                                                   a.factor, esum, want_energy);
+        stage<T, N, R2, RMAX, R1, INV, false, false>(v, tile, tw, gin, gout, lb, es, w, t, fe, flw, scale,
+                                                     a.factor, esum, want_energy);
+        stage<T, N, R3, RMAX, R1 * R2, INV, false, true>(v, tile, tw, gin, gout, lb, es, w, t, fe, flw, scale,
+                                                         a.factor, esum, want_energy);
     }
     if (!want_energy) return;
 
@@ -457,20 +411,20 @@ int rmax_of(int N)
 // Elements per thread (elems_per_thread<T, N, YZ> on the host).
 int elems_of(int N, jfft_prec prec, bool yz)
 {
-    (void)prec;
     const int rmax = rmax_of(N);
     if (!yz) return rmax;
-    return std::min(std::max(N / 16, rmax), 16);
+    const int cap = prec == JFFT_C64 ? 16 : 32;
+    return std::min(std::max(N / 16, rmax), cap);
 }
 
-// Lines per tile of a pass (see the kernel's mapping): rows of up to 256
-// threads for the pass along x; for y and z, up to 256 bytes of consecutive
-// x (32 FP32 or 16 FP64 complex values) within 256 threads.
+// Lines per CTA of a pass (see the kernel's mapping): rows of about 256
+// threads for the pass along x; for y and z, 256 bytes of consecutive x
+// (32 FP32 or 16 FP64 complex values), at most 512 threads.
 int lines_per_cta(int axis, int N, const int n[3], jfft_prec prec)
 {
     const int tt = N / elems_of(N, prec, axis != 0);
     if (axis == 0) return std::max(1, std::min(256 / tt, n[1] * n[2]));
-    return std::max(1, std::min(std::min(prec == JFFT_C64 ? 16 : 32, n[0]), 256 / tt));
+    return std::max(1, std::min(std::min(prec == JFFT_C64 ? 16 : 32, n[0]), 512 / tt));
 }
 
 long long ctas_of_pass(int axis, const int n[3], int W)
@@ -527,29 +481,8 @@ jac_status check_shape(int n1, int n2, int n3, jfft_prec prec)
 }  // namespace
 
 // Launch of one pass: the kernel instantiation for (T, N, INV).
-// CTAs that fit one SM at once for a kernel, block size and shared memory
-// (cached per kernel and device).
-int resident_ctas(const void *kern, int block, size_t smem)
-{
-    static std::mutex mu;
-    static std::vector<std::pair<std::pair<const void *, int>, int>> cache;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    std::lock_guard<std::mutex> lk(mu);
-    for (const auto &c : cache)
-        if (c.first.first == kern && c.first.second == dev) return c.second;
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (void (*)(PassArgs))kern, block, smem) != cudaSuccess ||
-        nb < 1)
-        nb = 1;
-    cache.push_back({{kern, dev}, nb});
-    return nb;
-}
-
-// Launch of one pass: the kernel instantiation for (T, N, INV, YZ), with
-// as many CTAs as fit the GPU at once (at most one per tile).
 template <typename T, bool INV, bool YZ>
-jac_status launch_pass_t(int N, const PassArgs &a, unsigned &grid, unsigned block, cudaStream_t st)
+jac_status launch_pass_t(int N, const PassArgs &a, unsigned grid, unsigned block, cudaStream_t st)
 {
     size_t smem = 0;
     void (*kern)(PassArgs) = nullptr;
@@ -558,7 +491,7 @@ jac_status launch_pass_t(int N, const PassArgs &a, unsigned &grid, unsigned bloc
     case NN:                                                                                                \
         kern = k_fft_pass<T, NN, INV, YZ>;                                                                  \
         smem = (Radix<NN>::R2 > 1 ? (size_t)a.W * row_stride<T, NN>() * sizeof(C2<T>) : 0) +               \
-               (size_t)NN * sizeof(C2<T>) + (size_t)NN * sizeof(T);                                         \
+               (size_t)NN * sizeof(C2<T>) + (size_t)NN * sizeof(T) + (size_t)a.W * sizeof(T);               \
         break;
         JFFT_CASE(2) JFFT_CASE(4) JFFT_CASE(8) JFFT_CASE(16) JFFT_CASE(32) JFFT_CASE(64) JFFT_CASE(128)
         JFFT_CASE(256) JFFT_CASE(512) JFFT_CASE(1024)
@@ -588,8 +521,6 @@ jac_status launch_pass_t(int N, const PassArgs &a, unsigned &grid, unsigned bloc
             else it->second = smem;
         }
     }
-    const long long fit = (long long)resident_ctas((const void *)kern, (int)block, smem) * jac::device_sm_count();
-    grid = (unsigned)std::min<long long>(a.ntiles, fit);
     kern<<<grid, block, smem, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -670,8 +601,7 @@ jac_status run3(jfft_plan *p, const void *in, void *out, bool inv, double scale,
             a.energy = energy;
             a.partials = reinterpret_cast<double *>(p->ws + p->L.partials);
         }
-        a.ntiles = (int)jfft::ctas_of_pass(axis, p->n, a.W);
-        unsigned grid = 0;
+        const unsigned grid = (unsigned)jfft::ctas_of_pass(axis, p->n, a.W);
         const unsigned block = (unsigned)jfft::threads_of_pass(N, a.W, p->prec, axis != 0);
         jac_status s;
         const bool yz = axis != 0;
