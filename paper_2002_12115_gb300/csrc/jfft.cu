@@ -141,15 +141,23 @@ struct Radix {
 
 // Elements of a line each thread holds.  The pass along x keeps the
 // largest radix (more lanes along each row); the passes along y and z take
-// up to 32 (FP32) or 16 (FP64) so that fewer threads serve a line and a CTA
-// of at most 512 threads covers 256 bytes of consecutive x.
+// up to 16, so that fewer threads serve a line and a CTA of at most 512
+// threads covers up to 256 bytes of consecutive x.
 template <typename T, int N, bool YZ>
 __host__ __device__ constexpr int elems_per_thread()
 {
     constexpr int rmax = Radix<N>::RMAX;
-    constexpr int cap = sizeof(T) == 4 ? 32 : 16;
     constexpr int want = N / 16 > rmax ? N / 16 : rmax;
-    return YZ ? (want < cap ? want : cap) : rmax;
+    return YZ ? (want < 16 ? want : 16) : rmax;
+}
+
+// CTAs per SM the kernel is built for: two for the FP32 passes along y and z
+// (at most 64 registers a thread), so that one CTA's loads overlap the
+// other's butterflies.
+template <typename T, bool YZ>
+__host__ __device__ constexpr int min_ctas_per_sm()
+{
+    return (sizeof(T) == 4 && YZ) ? 2 : 1;
 }
 
 // Shared-memory index of element e of a line: one pad element after every
@@ -269,7 +277,7 @@ __device__ __forceinline__ void stage(C2<T> (&v)[RMAX], C2<T> *tile, const C2<T>
 }
 
 template <typename T, int N, bool INV, bool YZ>
-__global__ void __launch_bounds__(512) k_fft_pass(const PassArgs a)
+__global__ void __launch_bounds__(512, min_ctas_per_sm<T, YZ>()) k_fft_pass(const PassArgs a)
 {
     using RX = Radix<N>;
     constexpr int RMAX = elems_per_thread<T, N, YZ>();   // elements per thread
@@ -411,10 +419,10 @@ int rmax_of(int N)
 // Elements per thread (elems_per_thread<T, N, YZ> on the host).
 int elems_of(int N, jfft_prec prec, bool yz)
 {
+    (void)prec;
     const int rmax = rmax_of(N);
     if (!yz) return rmax;
-    const int cap = prec == JFFT_C64 ? 16 : 32;
-    return std::min(std::max(N / 16, rmax), cap);
+    return std::min(std::max(N / 16, rmax), 16);
 }
 
 // Lines per CTA of a pass (see the kernel's mapping): rows of about 256
