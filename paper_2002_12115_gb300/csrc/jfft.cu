@@ -217,7 +217,7 @@ __global__ void k_fft_factors(double c, int n1, int n2, int n3, T *f1, T *f2, T 
 template <typename T, int N, int R, int RMAX, int NS, bool INV, bool FIRST, bool LAST>
 __device__ __forceinline__ void stage(C2<T> (&v)[RMAX], C2<T> *tile, const C2<T> *tw, const C2<T> *gin, C2<T> *gout,
                                       long long lb, long long es, int w, int t, const T *fe, T fl, T scale,
-                                      bool factor, double &esum, bool want_energy)
+                                      bool factor, T &esum, bool want_energy)
 {
     constexpr int TT = N / RMAX;       // threads per line
     constexpr int BPT = RMAX / R;      // butterflies per thread
@@ -253,7 +253,7 @@ __device__ __forceinline__ void stage(C2<T> (&v)[RMAX], C2<T> *tile, const C2<T>
         }
         Dif<T, R, R / 2, INV>::run(&v[q * R]);
     }
-    T e_loc = (T)0;     // this thread's |u|^2, summed in T over its at most 16 outputs
+    T e_loc = (T)0;     // this thread's |u|^2, summed in T over its outputs
 #pragma unroll
     for (int q = 0; q < BPT; ++q) {
         const int j = t + q * TT;
@@ -272,7 +272,7 @@ __device__ __forceinline__ void stage(C2<T> (&v)[RMAX], C2<T> *tile, const C2<T>
             }
         }
     }
-    if constexpr (LAST) esum += (double)e_loc;
+    if constexpr (LAST) esum += e_loc;
     if constexpr (!LAST) __syncthreads();
 }
 
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(512, min_ctas_per_sm<T, YZ>()) k_fft_pass(cons
     const bool want_energy = a.energy != nullptr;
     const T scale = (T)a.scale;
     const T flw = a.factor ? fl[w] : (T)1;
-    double esum = 0.0;
+    T esum = (T)0;
     C2<T> v[RMAX];
     constexpr int R1 = RX::R1, R2 = RX::R2, R3 = RX::R3;
     if constexpr (R2 == 1) {
@@ -352,52 +352,57 @@ __global__ void __launch_bounds__(512, min_ctas_per_sm<T, YZ>()) k_fft_pass(cons
     }
     if (!want_energy) return;
 
-    // energy: block sum (warp shuffles when the block is whole warps, else
-    // one thread in thread order) into this CTA's partial; k_fft_energy adds
-    // the partials in CTA order after the pass
-    int nred = blockDim.x;
+    // energy: a pairwise tree over the block in T (warp shuffles, then the
+    // warps' sums in shared memory; log2 of the block's size roundings, and
+    // FP64 only for the CTA's one partial -- GB300's FP64 pipe is narrow);
+    // k_fft_energy adds the partials after the pass
+    __shared__ T tred[32];
+    T v_e = esum;
     if ((blockDim.x & 31) == 0) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) esum += __shfl_down_sync(0xffffffffu, esum, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = esum;
-        nred = blockDim.x >> 5;
-    } else {
-        red[threadIdx.x] = esum;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < nred; ++i) s += red[i];
-        a.partials[blockIdx.x] = s;
+        for (int o = 16; o > 0; o >>= 1) v_e += __shfl_down_sync(0xffffffffu, v_e, o);
+        if ((threadIdx.x & 31) == 0) tred[threadIdx.x >> 5] = v_e;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int nw = blockDim.x >> 5;
+            T x = threadIdx.x < nw ? tred[threadIdx.x] : (T)0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if (threadIdx.x == 0) a.partials[blockIdx.x] = (double)x;
+        }
+    } else {                                   // blocks of fewer than 32 threads (short lines)
+        red[threadIdx.x] = (double)v_e;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sum = 0.0;
+            for (unsigned i = 0; i < blockDim.x; ++i) sum += red[i];
+            a.partials[blockIdx.x] = sum;
+        }
     }
 }
 
 // Sum of the n per-CTA energy partials of the last pass, in a fixed order:
-// thread t adds the partials t, t + blockDim, ... (Neumaier), then thread 0
-// adds the threads' sums in thread order.  One CTA of 512 threads.
+// thread t adds the partials t, t + 512, ... (four independent loads in
+// flight), then a pairwise tree over the 512 threads.  One CTA of 512
+// threads.
 __global__ void __launch_bounds__(512) k_fft_energy(const double *__restrict__ partials, int n, double *energy)
 {
     __shared__ double red[512];
-    double s = 0.0, comp = 0.0;
-#pragma unroll 4
-    for (int b = threadIdx.x; b < n; b += blockDim.x) {
-        const double x = partials[b];
-        const double tsum = s + x;
-        comp += fabs(s) >= fabs(x) ? (s - tsum) + x : (x - tsum) + s;
-        s = tsum;
+    const int t = threadIdx.x;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    for (int b = t; b < n; b += 4 * 512) {
+        s0 += partials[b];
+        if (b + 512 < n) s1 += partials[b + 512];
+        if (b + 1024 < n) s2 += partials[b + 1024];
+        if (b + 1536 < n) s3 += partials[b + 1536];
     }
-    red[threadIdx.x] = s + comp;
+    red[t] = (s0 + s1) + (s2 + s3);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double e = 0.0, ec = 0.0;
-        for (unsigned i = 0; i < blockDim.x; ++i) {
-            const double x = red[i];
-            const double tsum = e + x;
-            ec += fabs(e) >= fabs(x) ? (e - tsum) + x : (x - tsum) + e;
-            e = tsum;
-        }
-        *energy = e + ec;
+    for (int h = 256; h > 0; h >>= 1) {
+        if (t < h) red[t] += red[t + h];
+        __syncthreads();
     }
+    if (t == 0) *energy = red[0];
 }
 
 // ---------------------------------------------------------------- host
