@@ -456,7 +456,7 @@ def bench_single(args, w, stream):
             "residual": gosa, "jac": jac, "dev": dev, "host": host, "p": p_dev, "clocks": clk.summary()}
 
 
-def bench_e2e(args, w, jac, stream, want_residual, host_t, f32_host=False):
+def bench_e2e(args, w, jac, stream, want_residual, fields_t, f32_host=False):
     """The same step through the C ABI from pinned host buffers: every step
     copies its thirteen inputs in, sweeps, and copies the state and the
     residual out, all inside the timed region.  f32_host: the inputs as FP32
@@ -478,14 +478,14 @@ def bench_e2e(args, w, jac, stream, want_residual, host_t, f32_host=False):
     if f32_host:
         # the inputs as FP32 numbers (what FP32 storage holds), in pinned memory
         host = {}
-        for k, v in host_t.items():
+        for k, v in fields_t.items():
             t = torch.empty(v.shape, dtype=torch.float32, pin_memory=True)
-            t.copy_(v)
+            t.copy_(v.float())
             host[k] = t.numpy()
         p_host = [torch.empty((K, J, I), dtype=torch.float32, pin_memory=True).numpy() for _ in range(2)]
     else:
         host = {}
-        for k, v in host_t.items():                          # pinned FP64 inputs
+        for k, v in fields_t.items():                        # pinned FP64 inputs
             t = torch.empty(v.shape, dtype=torch.float64, pin_memory=True)
             t.copy_(v)
             host[k] = t.numpy()
@@ -992,14 +992,14 @@ def run_native(args, w, wname):
 
     I, J, K, n, prec = w["I"], w["J"], w["K"], w["sweeps"], w["prec"]
     want_oracle = rank == 0 and not (args.no_parity and args.no_cpu_baseline)
-    args.need_host = (not args.no_e2e) or want_oracle
+    args.need_host = want_oracle            # FP64 host copies: the oracle's inputs (rank 0)
     s = bench_single(args, w, stream)
     units = n_interior(w) * n * args.steps / 1e9
     value, ms = replica_value(units, s["ms"], world, args.dist)
     e2e = None
     f32_host = prec != "f64"
     if not args.no_e2e:
-        e2e_ms = bench_e2e(args, w, s["jac"], stream, s["residual"], s["host"], f32_host=f32_host)
+        e2e_ms = bench_e2e(args, w, s["jac"], stream, s["residual"], s["dev"], f32_host=f32_host)
         e2e, e2e_ms = replica_value(units, e2e_ms, world, args.dist)
     p_gpu = s["p"].cpu().numpy()          # state after the last timed step
     gosa = s["residual"]

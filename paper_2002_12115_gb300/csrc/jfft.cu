@@ -151,13 +151,14 @@ __host__ __device__ constexpr int elems_per_thread()
     return YZ ? (want < 16 ? want : 16) : rmax;
 }
 
-// CTAs per SM the kernel is built for: two for the FP32 passes along y and z
-// (at most 64 registers a thread), so that one CTA's loads overlap the
-// other's butterflies.
+// CTAs per SM the kernel is built for: for FP32, two 512-thread CTAs of the
+// passes along y and z and four 256-thread CTAs of the pass along x (at
+// most 64 registers a thread), so that one CTA's loads overlap another's
+// butterflies; FP64 (bound by its ALU) keeps the registers it wants.
 template <typename T, bool YZ>
 __host__ __device__ constexpr int min_ctas_per_sm()
 {
-    return (sizeof(T) == 4 && YZ) ? 2 : 1;
+    return sizeof(T) == 4 ? (YZ ? 2 : 4) : 1;
 }
 
 // Shared-memory index of element e of a line: one pad element after every
@@ -277,7 +278,7 @@ __device__ __forceinline__ void stage(C2<T> (&v)[RMAX], C2<T> *tile, const C2<T>
 }
 
 template <typename T, int N, bool INV, bool YZ>
-__global__ void __launch_bounds__(512, min_ctas_per_sm<T, YZ>()) k_fft_pass(const PassArgs a)
+__global__ void __launch_bounds__(YZ ? 512 : 256, min_ctas_per_sm<T, YZ>()) k_fft_pass(const PassArgs a)
 {
     using RX = Radix<N>;
     constexpr int RMAX = elems_per_thread<T, N, YZ>();   // elements per thread
