@@ -773,6 +773,10 @@ def bench_adjoint(args, w, stream, steps=3):
 
 
 FFT_BYTES_PER_POINT = {"c32": 3 * 2 * 8, "c64": 3 * 2 * 16}   # three passes, each reads and writes every point
+# FP64 operations (DADD + DMUL + DFMA, ncu-counted) per point of one spectral
+# step of the FP64 FFT (three passes), by grid; the FP64 path is bound by
+# GB300's FP64 pipe, not by HBM (profiles/k_fft_pass_512cube.md)
+FFT_C64_OPS_PER_POINT = {(512, 512, 512): 96.9}
 
 
 def bench_fft(args, w, stream, steps=None, warmup=None, e2e=True, parity=True):
@@ -813,13 +817,20 @@ def bench_fft(args, w, stream, steps=None, warmup=None, e2e=True, parity=True):
         gpts = N / (ms * 1e-3) / 1e9
         peak, kind = measured_peak()
         achieved = FFT_BYTES_PER_POINT[prec] * N / (ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_kind": kind, "bytes_per_point": FFT_BYTES_PER_POINT[prec],
+                "kernel": "k_fft_pass (3 passes per step, plus the factor and energy kernels)"}
+        ops = FFT_C64_OPS_PER_POINT.get((n1, n2, n3)) if prec == "c64" else None
+        if ops:
+            ach = ops * N / (ms * 1e-3) / 1e9
+            alu = f64_alu_peak_gops()
+            roof = {"bound": "alu", "achieved": ach, "peak": alu, "unit": "G FP64 op/s", "frac": ach / alu,
+                    "peak_kind": "derived: 2 FP64 ops per SM per clock x 152 SMs x max SM clock",
+                    "ops_per_point": ops, "hbm_frac": achieved / peak,
+                    "kernel": "k_fft_pass (3 passes per step, plus the factor and energy kernels)"}
         out.update({"value": gpts, "unit": "Gpoint/s (3-D FFT spectral steps)", "ms_per_step": ms,
                     "grid": [n1, n2, n3], "prec": prec, "energy": float(energy.item()),
-                    "gflops_5nlogn": 5 * N * np.log2(N) / (ms * 1e-3) / 1e9,
-                    "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                                 "frac": achieved / peak, "peak_kind": kind,
-                                 "bytes_per_point": FFT_BYTES_PER_POINT[prec],
-                                 "kernel": "k_fft_pass (3 passes per step, plus the factor and energy kernels)"}})
+                    "gflops_5nlogn": 5 * N * np.log2(N) / (ms * 1e-3) / 1e9, "roofline": roof})
         if e2e:
             host_u0 = torch.empty(u0.shape, dtype=cdt, pin_memory=True)
             host_u0.copy_(u0)
