@@ -8,40 +8,33 @@
 //
 // Kernel design (persistent, warp-specialised, one CTA per SM, all passes of
 // a call in one cooperative launch):
-//   * an item is a tile of 128 columns x R2 = 8 rows in (i, j) of output
-//     points over `kdepth` output planes kb .. ke-1.  Sweep 1 runs over the
-//     tile's 128 columns, the R1 = R2 + 2 rows j0-1 .. j0+R2 and the planes
-//     kb-1 .. ke; sweep 2 over the R2 inner rows and planes kb .. ke-1, and
-//     it is valid on columns i0+1 .. i0+126 (its neighbours must lie in
-//     sweep 1's columns), so tiles advance by 124 columns and overlap.  A
-//     tile owns (stores, and counts in the residual) columns i0+1 .. i0+124,
-//     the last tile of a row up to I-2.  When the column past the tile is
-//     the face I-1, its value never changes, and lane 31 keeps it from
-//     sweep 1's state reads, so the last tile reaches column I-2 = i0+127;
-//   * warp 10 (one lane) copies the planes of p_t, with a halo of 4 columns
-//     and 2 rows, into a ring of 4 slots; before pass t >= 1 it waits on the
-//     grid barrier of the pass before;
-//   * warp 11 (one lane) copies the twelve coefficient tiles (128 x R1) of
-//     every sweep-1 plane into a ring of 3 stages.  A stage serves sweep 1
-//     at plane m and, one step later, sweep 2 at plane m, so it is released
-//     only after both;
+//   * an item is a tile of the 128 columns i0 .. i0+127 (i0 a multiple of
+//     128) x R2 = 8 rows in (i, j) of output points over `kdepth` output
+//     planes kb .. ke-1.  Sweep 1 runs over the tile's columns, the
+//     R1 = R2 + 2 rows j0-1 .. j0+R2 and the planes kb-1 .. ke; sweep 2 over
+//     the R2 inner rows and planes kb .. ke-1.  Tiles do not overlap: sweep 2
+//     at columns i0 and i0+127 needs sweep 1 at columns i0-1 and i0+128 too;
+//   * warp 10 (one lane) copies, in the order they are used, the planes of
+//     p_t with a halo of 4 columns and 2 rows into a ring of 4 slots, and the
+//     twelve coefficient tiles (128 x R1) of every sweep-1 plane into a ring
+//     of 3 stages.  A stage serves sweep 1 at plane m and, one step later,
+//     sweep 2 at plane m, so it is released only after both.  Before the
+//     state of pass t >= 1 it waits on the grid barrier of the pass before;
 //   * consumer warp w (0 .. R1-1) owns row j0-1+w.  At step s (plane
 //     m = kb-1+s) it computes sweep 1 there into a ring of 4 intermediate
 //     planes, and (warps 1 .. R1-2, s >= 2) sweep 2 at plane m-1 from the
 //     intermediate planes m-2 .. m, which every warp has written (an
 //     mbarrier per intermediate plane);
+//   * warp 11 (the edge warp, 20 lanes) computes sweep 1 at columns i0-1 and
+//     i0+128 of the R1 rows at every step, from the state ring and
+//     coefficients it loads from global memory one plane ahead (those
+//     columns belong to the neighbouring tiles, whose CTAs copy them at
+//     about the same time);
 //   * the residual of the last pass's second sweep is reduced as in the
 //     single-sweep kernel; every wait is bounded.
 //
-// Measured on GB300 against the single-sweep kernel (FP32, Gpoint-updates/s):
-// 129x129x257 126 against 129, 513x513x1025 110 against 114, 257x257x513 88
-// against 119 (three 128-column tiles per 257-point row leave a third of the
-// lanes idle).  On 129x129x257 a pass moves 98 MB per sweep from DRAM against
-// 187 MB, but it executes 17% more instructions (halo rows and planes) and
-// waits at every step for all warps' intermediate rows, so it is bound by
-// latency at 47% issue; the shared memory holds one 61 KB coefficient stage
-// in flight.  An L2 prefetch of the stages ahead and per-row barriers were
-// both slower.  The library therefore runs single sweeps unless asked.
+// Twelve warps leave 168 registers a thread (a thirteenth would put four
+// warps on one SM sub-partition and cap them at 128).
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -55,7 +48,6 @@ namespace jac {
 struct Sweep2Shape {
     static constexpr int VI = 4, TI = 128, H = 4;
     static constexpr int R2 = 8, R1 = R2 + 2;                // output rows, sweep-1 rows (= consumer warps)
-    static constexpr int ADV = TI - 4;                       // tile advance in i
     static constexpr int PW = TI + 2 * H, PH = R1 + 2;       // state plane box
     static constexpr int P_BYTES = PW * PH * 4;              // 6528
     static constexpr int TILE = TI * R1 * 4;                 // one coefficient tile, 5120
@@ -63,6 +55,7 @@ struct Sweep2Shape {
     static constexpr int Q_BYTES = TI * R1 * 4;              // one intermediate plane
     static constexpr int RP = 4, RC = 3, RQ = 4;
     static constexpr size_t SMEM = (size_t)RP * P_BYTES + (size_t)RQ * Q_BYTES + (size_t)RC * C_BYTES + 128;
+    static constexpr int EDGE_WARP = R1 + 1;                 // sweep 1 at the two columns past the tile
     static constexpr int THREADS = 32 * (R1 + 2);
     static_assert(P_BYTES % 128 == 0 && Q_BYTES % 128 == 0 && C_BYTES % 128 == 0, "slot alignment");
 };
@@ -70,6 +63,7 @@ struct Sweep2Shape {
 struct Sweep2Desc {
     CUtensorMap p[2];          // state buffers, box (PW, PH, 1)
     CUtensorMap coef[12];      // JAC_A0 .. JAC_BND (index q-1), box (TI, R1, 1)
+    const float *coef_ptr[12]; // the same arrays, for the edge warp's loads
     void *p_buf[2];
     int I, J, K, pitch;
     int kdepth, nti, ntj, nkb, nitems;
@@ -97,7 +91,7 @@ __device__ __forceinline__ Item2 decode_item2(const Sweep2Desc &d, int item)
     const int r = item / d.ntj;
     it.ti = r % d.nti;
     const int kk = r / d.nti;
-    it.i0 = it.ti * S::ADV;
+    it.i0 = it.ti * S::TI;
     it.j0 = 1 + tj * S::R2;
     it.kb = 1 + kk * d.kdepth;
     it.nout = min(d.K - 1, it.kb + d.kdepth) - it.kb;
@@ -130,42 +124,77 @@ k_sweep2(const __grid_constant__ Sweep2Desc d, const Sweep2Args a)
         cons_bar;
     __shared__ volatile int s_abort;
     __shared__ double s_part[R1];
+    __shared__ float q_edge[RQ][R1][2];   // sweep-1 values at columns i0-1 and i0+128, per row
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int G = gridDim.x;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < RP; ++s) { mbar_init(&p_full[s], 1); mbar_init(&p_empty[s], R1); }
+        for (int s = 0; s < RP; ++s) { mbar_init(&p_full[s], 1); mbar_init(&p_empty[s], R1 + 1); }
         for (int s = 0; s < RC; ++s) { mbar_init(&c_full[s], 1); mbar_init(&c_empty[s], R1); }
-        for (int s = 0; s < RQ; ++s) { mbar_init(&q_full[s], R1); mbar_init(&q_empty[s], R1); }
+        for (int s = 0; s < RQ; ++s) { mbar_init(&q_full[s], R1 + 1); mbar_init(&q_empty[s], R1); }
         mbar_init(&cons_bar, R1);
         s_abort = 0;
         fence_mbar_init();
     }
     __syncthreads();
 
-    if (warp == R1 + 1) {
-        // ------------------------------------------------ coefficient producer
+    if (warp == R1) {
+        // ------------------------------------------------------------ producer
+        // One lane copies, per item, the coefficient stage of each sweep-1
+        // plane (twelve 128 x R1 tiles) and the state planes of p_t with a
+        // halo of 4 columns and 2 rows, in the order the consumers use them:
+        // state planes 0 and 1, then per step s state plane s+2 and stage
+        // s+1.  Before the state of pass t >= 1 it waits on the grid barrier
+        // of the pass before (the first stage of the pass does not need it).
         if (lane == 0) {
-            const uint64_t pol = l2_policy(a.l2_keep_state ? -1 : 0);
+            const uint64_t pol_c = l2_policy(a.l2_keep_state ? -1 : 0);
             const uint64_t pol_keep = l2_policy(1);
-            uint32_t cc = 0;
+            const uint64_t pol_p = l2_policy(a.l2_keep_state ? 1 : 0);
+            uint32_t pc = 0, cc = 0;
             bool ok = true;
-            for (int t = 0; t < a.n_pass && ok; ++t)
+            const CUtensorMap *pm = nullptr;
+            auto put_state = [&](const Item2 &it, int q) -> bool {
+                const uint32_t slot = pc % RP, use = pc / RP;
+                if (use > 0 && !mbar_wait_bounded(&p_empty[slot], (use - 1) & 1)) return false;
+                if (s_abort) return false;
+                mbar_arrive_expect_tx(&p_full[slot], (uint32_t)S::P_BYTES);
+                tma_load_3d_hint(base + (size_t)slot * S::P_BYTES, pm, &p_full[slot], it.i0 - H, it.j0 - 2,
+                                 it.kb - 2 + q, pol_p);
+                ++pc;
+                return true;
+            };
+            auto put_coef = [&](const Item2 &it, int q) -> bool {
+                const uint32_t slot = cc % RC, use = cc / RC;
+                if (use > 0 && !mbar_wait_bounded(&c_empty[slot], (use - 1) & 1)) return false;
+                if (s_abort) return false;
+                unsigned char *st = ring_c + (size_t)slot * S::C_BYTES;
+                mbar_arrive_expect_tx(&c_full[slot], (uint32_t)S::C_BYTES);
+                for (int k = JAC_A0; k <= JAC_BND; ++k)
+                    tma_load_3d_hint(st + (size_t)(k - 1) * S::TILE, &d.coef[k - 1], &c_full[slot], it.i0,
+                                     it.j0 - 1, it.kb - 1 + q, ((a.l2_keep_coef >> k) & 1u) ? pol_keep : pol_c);
+                ++cc;
+                return true;
+            };
+            for (int t = 0; t < a.n_pass && ok; ++t) {
+                pm = ((t + a.par) & 1) ? &d.p[1] : &d.p[0];
+                bool first = true;
                 for (int item = blockIdx.x; item < d.nitems && ok; item += G) {
                     const Item2 it = decode_item2(d, item);
-                    for (int q = 0; q < it.nout + 2; ++q, ++cc) {
-                        const uint32_t slot = cc % RC, use = cc / RC;
-                        if (use > 0 && !mbar_wait_bounded(&c_empty[slot], (use - 1) & 1)) { ok = false; break; }
-                        if (s_abort) { ok = false; break; }
-                        unsigned char *st = ring_c + (size_t)slot * S::C_BYTES;
-                        mbar_arrive_expect_tx(&c_full[slot], (uint32_t)S::C_BYTES);
-                        for (int k = JAC_A0; k <= JAC_BND; ++k)
-                            tma_load_3d_hint(st + (size_t)(k - 1) * S::TILE, &d.coef[k - 1], &c_full[slot], it.i0,
-                                             it.j0 - 1, it.kb - 1 + q, ((a.l2_keep_coef >> k) & 1u) ? pol_keep : pol);
+                    if (!(ok = put_coef(it, 0))) break;
+                    if (t > 0 && first) {
+                        if (!(ok = wait_counter_bounded(&a.hdr->gbar, (unsigned)t * G))) break;
+                        fence_proxy_async_global();
+                    }
+                    first = false;
+                    if (!(ok = put_state(it, 0) && put_state(it, 1))) break;
+                    for (int q = 0; q < it.nout + 2 && ok; ++q) {
+                        ok = put_state(it, q + 2);
+                        if (ok && q + 1 < it.nout + 2) ok = put_coef(it, q + 1);
                     }
                 }
+            }
             if (!ok) {
                 s_abort = 1;
                 atomicExch(&a.hdr->errword, (int)JAC_ETIMEOUT);
@@ -174,39 +203,96 @@ k_sweep2(const __grid_constant__ Sweep2Desc d, const Sweep2Args a)
                 const uint32_t last = cc - 1 - ((cc - 1 - s) % RC);
                 (void)mbar_wait_bounded(&c_full[s], (last / RC) & 1);
             }
-        }
-    } else if (warp == R1) {
-        // ------------------------------------------------------ state producer
-        if (lane == 0) {
-            const uint64_t pol = l2_policy(a.l2_keep_state ? 1 : 0);
-            uint32_t pc = 0;
-            bool ok = true;
-            for (int t = 0; t < a.n_pass && ok; ++t) {
-                if (t > 0) {
-                    if (!wait_counter_bounded(&a.hdr->gbar, (unsigned)t * G)) { ok = false; break; }
-                    fence_proxy_async_global();
-                }
-                const CUtensorMap *pm = ((t + a.par) & 1) ? &d.p[1] : &d.p[0];
-                for (int item = blockIdx.x; item < d.nitems && ok; item += G) {
-                    const Item2 it = decode_item2(d, item);
-                    for (int q = 0; q < it.nout + 4; ++q, ++pc) {
-                        const uint32_t slot = pc % RP, use = pc / RP;
-                        if (use > 0 && !mbar_wait_bounded(&p_empty[slot], (use - 1) & 1)) { ok = false; break; }
-                        if (s_abort) { ok = false; break; }
-                        mbar_arrive_expect_tx(&p_full[slot], (uint32_t)S::P_BYTES);
-                        tma_load_3d_hint(base + (size_t)slot * S::P_BYTES, pm, &p_full[slot], it.i0 - H, it.j0 - 2,
-                                         it.kb - 2 + q, pol);
-                    }
-                }
-            }
-            if (!ok) {
-                s_abort = 1;
-                atomicExch(&a.hdr->errword, (int)JAC_ETIMEOUT);
-            }
             for (uint32_t s = 0; s < (uint32_t)RP && s < pc; ++s) {
                 const uint32_t last = pc - 1 - ((pc - 1 - s) % RP);
                 (void)mbar_wait_bounded(&p_full[s], (last / RP) & 1);
             }
+        }
+    } else if (warp == S::EDGE_WARP) {
+        // ----------------------------------------------------------- edge warp
+        // Lane 2r + e (r < R1) computes sweep 1 at row j0-1+r and column
+        // i0-1 (e = 0) or i0+128 (e = 1), the neighbours that sweep 2 needs
+        // past the tile's 128 columns, with the consumers' arithmetic.  Its
+        // twelve coefficients come from global memory one plane ahead.
+        const int r = lane >> 1, side = lane & 1;
+        const bool act = lane < 2 * R1;
+        const float omega = (float)a.omega;
+        const int I = d.I, J = d.J, K = d.K, pitch = d.pitch;
+        const int x = side ? H + TI : H - 1;             // the column in the state box
+        const int r0 = r * S::PW, r1 = (r + 1) * S::PW, r2 = (r + 2) * S::PW;
+        uint32_t pc = 0, qc = 0;
+        bool ok = true;
+        for (int t = 0; t < a.n_pass && ok; ++t) {
+            for (int item = blockIdx.x; item < d.nitems && ok; item += G) {
+                const Item2 it = decode_item2(d, item);
+                const int j = it.j0 - 1 + r;
+                const int ie = side ? it.i0 + TI : it.i0 - 1;
+                const bool col_in = act && (j >= 1) && (j <= J - 2) && (ie >= 1) && (ie <= I - 2);
+                float cf[12], cn[12];
+                auto load_coef = [&](int m, float (&v)[12]) {
+                    if (col_in && m >= 1 && m <= K - 2) {
+                        const size_t off = ((size_t)m * J + (size_t)j) * (size_t)pitch + (size_t)ie;
+#pragma unroll
+                        for (int q = 0; q < 12; ++q) v[q] = __ldg(d.coef_ptr[q] + off);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 12; ++q) v[q] = 0.0f;
+                    }
+                };
+                load_coef(it.kb - 1, cf);
+                for (int s = 0; s < it.nout + 2; ++s) {
+                    const int m = it.kb - 1 + s;
+                    if (s == 0) {
+                        ok = mbar_wait_bounded(&p_full[pc % RP], (pc / RP) & 1) &&
+                             mbar_wait_bounded(&p_full[(pc + 1) % RP], ((pc + 1) / RP) & 1);
+                    }
+                    const uint32_t q2 = pc + s + 2;
+                    ok = ok && mbar_wait_bounded(&p_full[q2 % RP], (q2 / RP) & 1);
+                    const uint32_t qs = qc + s;
+                    if (qs >= RQ) ok = ok && mbar_wait_bounded(&q_empty[qs % RQ], ((qs / RQ) - 1) & 1);
+                    ok = __all_sync(0xffffffffu, ok && !s_abort);
+                    if (!ok) break;
+                    if (s + 1 < it.nout + 2) load_coef(m + 1, cn);
+                    if (act) {
+                        const float *Pm = reinterpret_cast<const float *>(base + (size_t)((pc + s) % RP) * S::P_BYTES);
+                        const float *Pk =
+                            reinterpret_cast<const float *>(base + (size_t)((pc + s + 1) % RP) * S::P_BYTES);
+                        const float *Pp = reinterpret_cast<const float *>(base + (size_t)(q2 % RP) * S::P_BYTES);
+                        const float c = Pk[r1 + x];
+                        float out = c;
+                        if (col_in && m >= 1 && m <= K - 2) {
+                            const float bij = ((Pk[r2 + x + 1] - Pk[r0 + x + 1]) - Pk[r2 + x - 1]) + Pk[r0 + x - 1];
+                            const float bjk = ((Pp[r2 + x] - Pm[r2 + x]) - Pp[r0 + x]) + Pm[r0 + x];
+                            const float bik = ((Pp[r1 + x + 1] - Pm[r1 + x + 1]) - Pp[r1 + x - 1]) + Pm[r1 + x - 1];
+                            const float ss = ss_f32<false>(c, Pk[r1 + x + 1], Pk[r1 + x - 1], Pk[r2 + x], Pk[r0 + x],
+                                                           Pp[r1 + x], Pm[r1 + x], bij, bjk, bik, cf[0], cf[1], cf[2],
+                                                           cf[3], cf[4], cf[5], cf[6], cf[7], cf[8], cf[9], cf[10],
+                                                           cf[11]);
+                            out = fmaf(omega, ss, c);
+                        }
+                        q_edge[qs % RQ][r][side] = out;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 12; ++q) cf[q] = cn[q];
+                    __syncwarp();
+                    if (lane == 0) {
+                        mbar_arrive(&q_full[qs % RQ]);            // the edge values of intermediate plane s
+                        mbar_arrive(&p_empty[(pc + s) % RP]);     // state plane m-1 is done
+                    }
+                }
+                if (!ok) break;
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&p_empty[(pc + it.nout + 2) % RP]);
+                    mbar_arrive(&p_empty[(pc + it.nout + 3) % RP]);
+                }
+                pc += it.nout + 4;
+                qc += it.nout + 2;
+            }
+        }
+        if (!ok) {
+            s_abort = 1;
+            atomicExch(&a.hdr->errword, (int)JAC_ETIMEOUT);
         }
     } else {
         // ------------------------------------------------------------ consumers
@@ -234,24 +320,23 @@ k_sweep2(const __grid_constant__ Sweep2Desc d, const Sweep2Args a)
                 const Item2 it = decode_item2(d, item);
                 const int j = it.j0 - 1 + w;
                 const int ib = it.i0 + VI * lane;
-                const bool last_ti = (it.ti == d.nti - 1);
-                const int own_hi = last_ti ? I - 2 : it.i0 + S::ADV;
                 const bool row1_in = (j >= 1) && (j <= J - 2);
                 bool in_i[VI], owned[VI];
 #pragma unroll
                 for (int e = 0; e < VI; ++e) {
                     in_i[e] = (ib + e >= 1) && (ib + e <= I - 2);
-                    owned[e] = do2 && row1_in && in_i[e] && (ib + e >= it.i0 + 1) && (ib + e <= own_hi);
+                    owned[e] = do2 && row1_in && in_i[e];
                 }
                 bool all_owned = true;
 #pragma unroll
                 for (int e = 0; e < VI; ++e) all_owned = all_owned && owned[e];
                 const int r0 = w * S::PW, r1 = (w + 1) * S::PW, r2 = (w + 2) * S::PW;   // rows j-1, j, j+1
                 const int cidx = w * TI + VI * lane;
-                // the face column I-1 just past the tile: its state never
-                // changes; lane 31 keeps it from sweep 1's reads, per plane
-                // (the last three planes) and row (j-1, j, j+1)
-                float fh[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+                // a3 S - 1 of this row's points at sweep 1's plane, carried to
+                // sweep 2 at the same plane one step later
+                float ec_cur[VI], ec_prev[VI];
+#pragma unroll
+                for (int e = 0; e < VI; ++e) ec_cur[e] = ec_prev[e] = 0.0f;
 
                 for (int s = 0; s < it.nout + 2; ++s) {
                     const int m = it.kb - 1 + s;                 // sweep-1 plane
@@ -306,18 +391,15 @@ k_sweep2(const __grid_constant__ Sweep2Desc d, const Sweep2Args a)
                             const float bij = ((ek2[e + 2] - ek0[e + 2]) - ek2[e]) + ek0[e];
                             const float bjk = ((vp2[e] - vm2[e]) - vp0[e]) + vm0[e];
                             const float bik = ((ep1[e + 2] - em1[e + 2]) - ep1[e]) + em1[e];
-                            const float ss = ss_f32<false>(c, ek1[e + 2], ek1[e], ek2[e + 1], ek0[e + 1], ep1[e + 1],
-                                                           em1[e + 1], bij, bjk, bik, ca0[e], ca1[e], ca2[e], ca3[e],
-                                                           cb0[e], cb1[e], cb2[e], cc0[e], cc1[e], cc2[e], cwk[e],
-                                                           cbn[e]);
+                            ec_cur[e] = a3s_minus_one<false>(ca3[e], ca0[e], ca1[e], ca2[e], cc0[e], cc1[e], cc2[e]);
+                            const float ss = ss_f32_ec(c, ek1[e + 2], ek1[e], ek2[e + 1], ek0[e + 1], ep1[e + 1],
+                                                       em1[e + 1], bij, bjk, bik, ca0[e], ca1[e], ca2[e], ca3[e],
+                                                       cb0[e], cb1[e], cb2[e], cc0[e], cc1[e], cc2[e], cwk[e], cbn[e],
+                                                       ec_cur[e]);
                             out[e] = (in1 && in_i[e]) ? fmaf(omega, ss, c) : c;
                         }
                         float *qrow = reinterpret_cast<float *>(ring_q + (size_t)(qs % RQ) * S::Q_BYTES) + w * TI;
                         *reinterpret_cast<float4 *>(qrow + VI * lane) = make_float4(out[0], out[1], out[2], out[3]);
-                        // face history: planes m-2, m-1, m at column i0+128
-                        fh[0][0] = fh[1][0]; fh[0][1] = fh[1][1]; fh[0][2] = fh[1][2];
-                        fh[1][0] = fh[2][0]; fh[1][1] = fh[2][1]; fh[1][2] = fh[2][2];
-                        fh[2][0] = ek0[VI + 1]; fh[2][1] = ek1[VI + 1]; fh[2][2] = ek2[VI + 1];
                     }
                     __syncwarp();
                     if (lane == 0) {
@@ -342,15 +424,17 @@ k_sweep2(const __grid_constant__ Sweep2Desc d, const Sweep2Args a)
                             const float *Qp = reinterpret_cast<const float *>(ring_q + (size_t)(qs % RQ) * S::Q_BYTES);
                             const unsigned char *cs = ring_c + (size_t)((cc + s - 1) % RC) * S::C_BYTES;
                             const int q0 = (w - 1) * TI, q1 = w * TI, q2r = (w + 1) * TI;
-                            // column i0-1 is never needed (column i0 is not owned);
-                            // column i0+128 only as the face I-1
+                            // columns i0-1 and i0+128 come from the edge warp
+                            const float(*Em)[2] = q_edge[(qc + s - 2) % RQ];
+                            const float(*Ek)[2] = q_edge[(qc + s - 1) % RQ];
+                            const float(*Ep)[2] = q_edge[qs % RQ];
                             float ek0[VI + 2], ek1[VI + 2], ek2[VI + 2], em1[VI + 2], ep1[VI + 2];
                             float vm0[VI], vm2[VI], vp0[VI], vp2[VI];
-                            q_ext(Qk + q0, lane, 0.f, fh[1][0], ek0);
-                            q_ext(Qk + q1, lane, 0.f, fh[1][1], ek1);
-                            q_ext(Qk + q2r, lane, 0.f, fh[1][2], ek2);
-                            q_ext(Qm + q1, lane, 0.f, fh[0][1], em1);
-                            q_ext(Qp + q1, lane, 0.f, fh[2][1], ep1);
+                            q_ext(Qk + q0, lane, Ek[w - 1][0], Ek[w - 1][1], ek0);
+                            q_ext(Qk + q1, lane, Ek[w][0], Ek[w][1], ek1);
+                            q_ext(Qk + q2r, lane, Ek[w + 1][0], Ek[w + 1][1], ek2);
+                            q_ext(Qm + q1, lane, Em[w][0], Em[w][1], em1);
+                            q_ext(Qp + q1, lane, Ep[w][0], Ep[w][1], ep1);
                             lds_vec<float, VI>(Qm + q0 + VI * lane, vm0);
                             lds_vec<float, VI>(Qm + q2r + VI * lane, vm2);
                             lds_vec<float, VI>(Qp + q0 + VI * lane, vp0);
@@ -377,10 +461,10 @@ k_sweep2(const __grid_constant__ Sweep2Desc d, const Sweep2Args a)
                                 const float bij = ((ek2[e + 2] - ek0[e + 2]) - ek2[e]) + ek0[e];
                                 const float bjk = ((vp2[e] - vm2[e]) - vp0[e]) + vm0[e];
                                 const float bik = ((ep1[e + 2] - em1[e + 2]) - ep1[e]) + em1[e];
-                                const float ss = ss_f32<false>(c, ek1[e + 2], ek1[e], ek2[e + 1], ek0[e + 1],
-                                                               ep1[e + 1], em1[e + 1], bij, bjk, bik, ca0[e], ca1[e],
-                                                               ca2[e], ca3[e], cb0[e], cb1[e], cb2[e], cc0[e], cc1[e],
-                                                               cc2[e], cwk[e], cbn[e]);
+                                const float ss = ss_f32_ec(c, ek1[e + 2], ek1[e], ek2[e + 1], ek0[e + 1], ep1[e + 1],
+                                                           em1[e + 1], bij, bjk, bik, ca0[e], ca1[e], ca2[e], ca3[e],
+                                                           cb0[e], cb1[e], cb2[e], cc0[e], cc1[e], cc2[e], cwk[e],
+                                                           cbn[e], ec_prev[e]);
                                 out[e] = owned[e] ? fmaf(omega, ss, c) : c;
                                 if (res && owned[e]) ss2 = fmaf(ss, ss, ss2);
                             }
@@ -401,6 +485,8 @@ k_sweep2(const __grid_constant__ Sweep2Desc d, const Sweep2Args a)
                         __syncwarp();
                         if (lane == 0) mbar_arrive(&c_empty[(cc + s - 1) % RC]);  // stage s-1: both sweeps done
                     }
+#pragma unroll
+                    for (int e = 0; e < VI; ++e) ec_prev[e] = ec_cur[e];
                 }
                 if (!ok) break;
                 // the item's last state planes, stage and intermediate planes
@@ -488,28 +574,35 @@ jac_status fail2(jac_status st, const std::string &msg)
 
 }  // namespace
 
-// Tiles in i: the smallest count whose last tile reaches column I-2, either
-// within sweep 2's valid columns (i0 + 126) or, when the column past the
-// tile is the face I-1, at i0 + 127.
+// Tiles in i: columns 128 n .. 128 n + 127, until one holds column I-2.
 int sweep2_tiles_i(int I)
 {
     using S = Sweep2Shape;
-    for (int n = 1;; ++n) {
-        const int i0 = (n - 1) * S::ADV;
-        if (i0 + 126 >= I - 2 || i0 + 128 == I - 1) return n;
-    }
+    return (I - 2) / S::TI + 1;
 }
 
+// Output planes per item: the depth that minimises the rounds of items over
+// `ctas` CTAs times the steps of an item (its planes, the two extra planes
+// of sweep 1 and about two steps of start-up); ties go to the shallower.
 int sweep2_kdepth(long cols, int nk, int ctas)
 {
-    // one round of items when it fits at a depth of at most 256, else 16
-    if (nk <= 1) return 1;
-    if (cols <= ctas) {
-        const long kblocks = ctas / cols;
-        const long kd = std::max<long>(2, (nk + kblocks - 1) / kblocks);
-        if (kd <= 256) return (int)std::min<long>(kd, nk);
+    if (nk <= 2) return std::max(nk, 1);
+    long best_cost = -1;
+    int best = 2;
+    int prev = -1;
+    for (int n = 1; n <= nk; ++n) {
+        const int kd = std::max(2, (nk + n - 1) / n);
+        if (kd == prev) continue;
+        prev = kd;
+        const long items = cols * (long)((nk + kd - 1) / kd);
+        const long rounds = (items + ctas - 1) / ctas;
+        const long cost = rounds * (long)(kd + 4);
+        if (best_cost < 0 || cost < best_cost || (cost == best_cost && kd < best)) {
+            best_cost = cost;
+            best = kd;
+        }
     }
-    return std::min(nk, 16);
+    return best;
 }
 
 size_t sweep2_workspace_bytes(const jac_grid *g)
@@ -544,10 +637,12 @@ jac_status sweep2_run(const jac_grid *g, int kdepth, int n_pass, double *d_resid
     for (int b = 0; b < 2; ++b)
         if ((s = encode_box_map(&d.p[b], g->p[b], 4, d.pitch, d.pitch, g->J, g->K, S::PW, S::PH)) != JAC_OK)
             return s;
-    for (int q = JAC_A0; q <= JAC_BND; ++q)
+    for (int q = JAC_A0; q <= JAC_BND; ++q) {
         if ((s = encode_box_map(&d.coef[q - 1], g->coef[q], 4, d.pitch, d.pitch, g->J, g->K, S::TI, S::R1)) !=
             JAC_OK)
             return s;
+        d.coef_ptr[q - 1] = static_cast<const float *>(g->coef[q]);
+    }
     const unsigned nblocks = (unsigned)std::min<long long>(items, sms);
     if (ws_bytes < kWsHeaderBytes + (size_t)nblocks * sizeof(double))
         return fail2(JAC_EINVAL, "workspace too small for the two-sweep launch");

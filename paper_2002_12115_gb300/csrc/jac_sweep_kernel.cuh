@@ -117,11 +117,12 @@ __device__ __forceinline__ float a3s_minus_one(float a3, float a0, float a1, flo
 // times (neighbour - centre), the three b brackets and wrk1, then
 // a3 * that + p (a3 S - 1) with a3 S - 1 exact; times bnd.  Shared by the
 // single-sweep and the two-sweep kernels, so that both round alike.
-template <bool EXACT_SUM>
-__device__ __forceinline__ float ss_f32(float c, float xp, float xm, float yp, float ym, float zp, float zm,
-                                        float bij, float bjk, float bik, float a0, float a1, float a2, float a3,
-                                        float b0, float b1, float b2, float c0, float c1, float c2, float wk,
-                                        float bnd)
+// ss_f32_ec takes ec = a3 S - 1 already formed (it depends only on the
+// coefficients, so a kernel that updates the same point twice forms it once).
+__device__ __forceinline__ float ss_f32_ec(float c, float xp, float xm, float yp, float ym, float zp, float zm,
+                                           float bij, float bjk, float bik, float a0, float a1, float a2, float a3,
+                                           float b0, float b1, float b2, float c0, float c1, float c2, float wk,
+                                           float bnd, float ec)
 {
     float d = wk;
     d = fmaf(a0, xp - c, d);
@@ -133,8 +134,17 @@ __device__ __forceinline__ float ss_f32(float c, float xp, float xm, float yp, f
     d = fmaf(b0, bij, d);
     d = fmaf(b1, bjk, d);
     d = fmaf(b2, bik, d);
-    const float ec = a3s_minus_one<EXACT_SUM>(a3, a0, a1, a2, c0, c1, c2);
     return fmaf(a3, d, c * ec) * bnd;
+}
+
+template <bool EXACT_SUM>
+__device__ __forceinline__ float ss_f32(float c, float xp, float xm, float yp, float ym, float zp, float zm,
+                                        float bij, float bjk, float bik, float a0, float a1, float a2, float a3,
+                                        float b0, float b1, float b2, float c0, float c1, float c2, float wk,
+                                        float bnd)
+{
+    return ss_f32_ec(c, xp, xm, yp, ym, zp, zm, bij, bjk, bik, a0, a1, a2, a3, b0, b1, b2, c0, c1, c2, wk, bnd,
+                     a3s_minus_one<EXACT_SUM>(a3, a0, a1, a2, c0, c1, c2));
 }
 
 __device__ __forceinline__ void neumaier_add(double &s, double &c, double x)

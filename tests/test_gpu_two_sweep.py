@@ -2,13 +2,16 @@
 sweeps through the same context API.  Each point-update of a pass is the
 arithmetic of a single sweep, so the state must be bitwise the same.  The
 residual sums each lane's (at most four) squares in FP32 before the FP64
-reduction; where tiles overlap, the two kernels give a lane different points,
-so those partial sums round differently (measured 1e-11 relative): the bar
-is 1e-9, far inside the workload's 1e-5.  The grids cover one and
-several 128-column tiles in i (tiles advance by 124; I = 129 and 253 put the
-face column I-1 just past a tile), ragged 8-row tiles in j and ragged
-k-blocks, the smallest grid, and sweep counts that leave 0 to 3 single
-sweeps after the passes (passes come in even numbers)."""
+reduction; the two kernels can give a lane different points (the
+single-sweep kernel's tiles are not always 128 columns), so those partial
+sums may round differently (measured 1e-11 relative): the bar is 1e-9, far
+inside the workload's 1e-5.  The grids cover one and several 128-column
+tiles in i (I = 129 puts the face column just past the only tile, I = 130
+and 258 leave one owned column in the last tile, I = 257 and 513 fill
+their tiles), ragged 8-row tiles in j and ragged k-blocks, a grid with more
+items than CTAs (513 x 513 x 65: some CTAs take two), the smallest grid, and
+sweep counts that leave 0 to 3 single sweeps after the passes (passes come
+in even numbers)."""
 import numpy as np
 import pytest
 
@@ -22,6 +25,7 @@ CASES = [
     ((129, 17, 23), 4), ((129, 17, 23), 5), ((129, 17, 23), 6), ((129, 17, 23), 7),
     ((65, 33, 20), 10), ((200, 19, 37), 9), ((257, 40, 30), 8), ((253, 12, 9), 4),
     ((513, 17, 12), 4), ((130, 9, 11), 4), ((3, 3, 3), 4), ((5, 6, 7), 6), ((129, 129, 257), 8),
+    ((258, 11, 9), 5), ((257, 20, 70), 7), ((513, 513, 65), 6),
 ]
 
 
