@@ -17,14 +17,20 @@
 //   * warp 10 (one lane) copies, in the order they are used, the planes of
 //     p_t with a halo of 4 columns and 2 rows into a ring of 4 slots, and the
 //     twelve coefficient tiles (128 x R1) of every sweep-1 plane into a ring
-//     of 3 stages.  A stage serves sweep 1 at plane m and, one step later,
-//     sweep 2 at plane m, so it is released only after both.  Before the
-//     state of pass t >= 1 it waits on the grid barrier of the pass before;
+//     of 2 stages, which sweep 1 alone uses.  Before the state of pass
+//     t >= 1 it waits on the grid barrier of the pass before;
 //   * consumer warp w (0 .. R1-1) owns row j0-1+w.  At step s (plane
 //     m = kb-1+s) it computes sweep 1 there into a ring of 4 intermediate
-//     planes, and (warps 1 .. R1-2, s >= 2) sweep 2 at plane m-1 from the
-//     intermediate planes m-2 .. m, which every warp has written (an
-//     mbarrier per intermediate plane);
+//     planes, then (warps 1 .. R1-2, s >= 3) sweep 2 at plane m-2 from the
+//     intermediate planes m-3 .. m-1.  Sweep 2 trails by two planes so that
+//     its wait (every row of plane m-1 written: an mbarrier per
+//     intermediate plane) is for work the other warps finished a step ago,
+//     not for the step in flight.  Its coefficients come from global memory
+//     (the tiles were copied for sweep 1 two steps earlier, so they are read
+//     from L2) into a 6 KB buffer per warp: each lane copies its own 12 x 16
+//     bytes with cp.async at the end of a step, for the next step's sweep 2,
+//     so the L2 latency is hidden behind sweep 1.  (Keeping the stages for
+//     three steps would need four 61 KB stages in flight.)
 //   * warp 11 (the edge warp, 20 lanes) computes sweep 1 at columns i0-1 and
 //     i0+128 of the R1 rows at every step, from the state ring and
 //     coefficients it loads from global memory one plane ahead (those
@@ -53,11 +59,14 @@ struct Sweep2Shape {
     static constexpr int TILE = TI * R1 * 4;                 // one coefficient tile, 5120
     static constexpr int C_BYTES = 12 * TILE;                // one stage
     static constexpr int Q_BYTES = TI * R1 * 4;              // one intermediate plane
-    static constexpr int RP = 4, RC = 3, RQ = 4;
-    static constexpr size_t SMEM = (size_t)RP * P_BYTES + (size_t)RQ * Q_BYTES + (size_t)RC * C_BYTES + 128;
+    static constexpr int B_BYTES = 12 * TI * 4;              // one warp's sweep-2 coefficients of one row
+    static constexpr int RP = 4, RC = 2, RQ = 4;
+    static constexpr size_t SMEM =
+        (size_t)RP * P_BYTES + (size_t)RQ * Q_BYTES + (size_t)RC * C_BYTES + (size_t)R2 * B_BYTES + 128;
     static constexpr int EDGE_WARP = R1 + 1;                 // sweep 1 at the two columns past the tile
     static constexpr int THREADS = 32 * (R1 + 2);
-    static_assert(P_BYTES % 128 == 0 && Q_BYTES % 128 == 0 && C_BYTES % 128 == 0, "slot alignment");
+    static_assert(P_BYTES % 128 == 0 && Q_BYTES % 128 == 0 && C_BYTES % 128 == 0 && B_BYTES % 128 == 0,
+                  "slot alignment");
 };
 
 struct Sweep2Desc {
@@ -110,6 +119,15 @@ __device__ __forceinline__ void q_ext(const float *row, int lane, float left, fl
     e[5] = (lane == 31) ? right : r;
 }
 
+// 16 bytes global -> shared without a register round trip (cached in L2
+// only); the copies of a thread complete at cp_async_wait_all.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 __global__ void __launch_bounds__(Sweep2Shape::THREADS, 1)
 k_sweep2(const __grid_constant__ Sweep2Desc d, const Sweep2Args a)
 {
@@ -120,6 +138,7 @@ k_sweep2(const __grid_constant__ Sweep2Desc d, const Sweep2Args a)
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(dsm2_raw) + 127) & ~uintptr_t(127));
     unsigned char *ring_q = base + (size_t)RP * S::P_BYTES;
     unsigned char *ring_c = ring_q + (size_t)RQ * S::Q_BYTES;
+    unsigned char *bufs2 = ring_c + (size_t)RC * S::C_BYTES;   // per sweep-2 warp
     __shared__ __align__(8) uint64_t p_full[RP], p_empty[RP], c_full[RC], c_empty[RC], q_full[RQ], q_empty[RQ],
         cons_bar;
     __shared__ volatile int s_abort;
@@ -149,7 +168,7 @@ k_sweep2(const __grid_constant__ Sweep2Desc d, const Sweep2Args a)
         // s+1.  Before the state of pass t >= 1 it waits on the grid barrier
         // of the pass before (the first stage of the pass does not need it).
         if (lane == 0) {
-            const uint64_t pol_c = l2_policy(a.l2_keep_state ? -1 : 0);
+            const uint64_t pol_c = l2_policy(0);   // sweep 2 reads the tiles again from L2
             const uint64_t pol_keep = l2_policy(1);
             const uint64_t pol_p = l2_policy(a.l2_keep_state ? 1 : 0);
             uint32_t pc = 0, cc = 0;
@@ -327,32 +346,39 @@ k_sweep2(const __grid_constant__ Sweep2Desc d, const Sweep2Args a)
                     in_i[e] = (ib + e >= 1) && (ib + e <= I - 2);
                     owned[e] = do2 && row1_in && in_i[e];
                 }
-                bool all_owned = true;
+                bool all_owned = true, any_owned = false;
 #pragma unroll
-                for (int e = 0; e < VI; ++e) all_owned = all_owned && owned[e];
+                for (int e = 0; e < VI; ++e) {
+                    all_owned = all_owned && owned[e];
+                    any_owned = any_owned || owned[e];
+                }
                 const int r0 = w * S::PW, r1 = (w + 1) * S::PW, r2 = (w + 2) * S::PW;   // rows j-1, j, j+1
                 const int cidx = w * TI + VI * lane;
-                // a3 S - 1 of this row's points at sweep 1's plane, carried to
-                // sweep 2 at the same plane one step later
-                float ec_cur[VI], ec_prev[VI];
+                float *buf2 = reinterpret_cast<float *>(bufs2 + (size_t)(do2 ? w - 1 : 0) * S::B_BYTES);
+                // a3 S - 1 of this row's points at the sweep-1 planes of the
+                // last two steps, carried to sweep 2 at those planes
+                float ec1[VI], ec2[VI];
 #pragma unroll
-                for (int e = 0; e < VI; ++e) ec_cur[e] = ec_prev[e] = 0.0f;
+                for (int e = 0; e < VI; ++e) ec1[e] = ec2[e] = 0.0f;
 
-                for (int s = 0; s < it.nout + 2; ++s) {
+                for (int s = 0; s < it.nout + 3; ++s) {
                     const int m = it.kb - 1 + s;                 // sweep-1 plane
-                    // ---- sweep 1 at plane m, row j, into intermediate plane s
-                    if (s == 0) {
-                        ok = mbar_wait_bounded(&p_full[pc % RP], (pc / RP) & 1) &&
-                             mbar_wait_bounded(&p_full[(pc + 1) % RP], ((pc + 1) / RP) & 1);
-                    }
-                    const uint32_t q2 = pc + s + 2;
-                    ok = ok && mbar_wait_bounded(&p_full[q2 % RP], (q2 / RP) & 1);
-                    ok = ok && mbar_wait_bounded(&c_full[(cc + s) % RC], ((cc + s) / RC) & 1);
                     const uint32_t qs = qc + s;
-                    if (qs >= RQ) ok = ok && mbar_wait_bounded(&q_empty[qs % RQ], ((qs / RQ) - 1) & 1);
-                    ok = __all_sync(0xffffffffu, ok && !s_abort);
-                    if (!ok) break;
-                    {
+                    float ec0[VI];
+#pragma unroll
+                    for (int e = 0; e < VI; ++e) ec0[e] = 0.0f;
+                    if (s < it.nout + 2) {
+                        // ---- sweep 1 at plane m, row j, into intermediate plane s
+                        if (s == 0) {
+                            ok = mbar_wait_bounded(&p_full[pc % RP], (pc / RP) & 1) &&
+                                 mbar_wait_bounded(&p_full[(pc + 1) % RP], ((pc + 1) / RP) & 1);
+                        }
+                        const uint32_t q2 = pc + s + 2;
+                        ok = ok && mbar_wait_bounded(&p_full[q2 % RP], (q2 / RP) & 1);
+                        ok = ok && mbar_wait_bounded(&c_full[(cc + s) % RC], ((cc + s) / RC) & 1);
+                        if (qs >= RQ) ok = ok && mbar_wait_bounded(&q_empty[qs % RQ], ((qs / RQ) - 1) & 1);
+                        ok = __all_sync(0xffffffffu, ok && !s_abort);
+                        if (!ok) break;
                         const float *Pm = reinterpret_cast<const float *>(base + (size_t)((pc + s) % RP) * S::P_BYTES);
                         const float *Pk =
                             reinterpret_cast<const float *>(base + (size_t)((pc + s + 1) % RP) * S::P_BYTES);
@@ -391,43 +417,47 @@ k_sweep2(const __grid_constant__ Sweep2Desc d, const Sweep2Args a)
                             const float bij = ((ek2[e + 2] - ek0[e + 2]) - ek2[e]) + ek0[e];
                             const float bjk = ((vp2[e] - vm2[e]) - vp0[e]) + vm0[e];
                             const float bik = ((ep1[e + 2] - em1[e + 2]) - ep1[e]) + em1[e];
-                            ec_cur[e] = a3s_minus_one<false>(ca3[e], ca0[e], ca1[e], ca2[e], cc0[e], cc1[e], cc2[e]);
+                            ec0[e] = a3s_minus_one<false>(ca3[e], ca0[e], ca1[e], ca2[e], cc0[e], cc1[e], cc2[e]);
                             const float ss = ss_f32_ec(c, ek1[e + 2], ek1[e], ek2[e + 1], ek0[e + 1], ep1[e + 1],
                                                        em1[e + 1], bij, bjk, bik, ca0[e], ca1[e], ca2[e], ca3[e],
                                                        cb0[e], cb1[e], cb2[e], cc0[e], cc1[e], cc2[e], cwk[e], cbn[e],
-                                                       ec_cur[e]);
+                                                       ec0[e]);
                             out[e] = (in1 && in_i[e]) ? fmaf(omega, ss, c) : c;
                         }
                         float *qrow = reinterpret_cast<float *>(ring_q + (size_t)(qs % RQ) * S::Q_BYTES) + w * TI;
                         *reinterpret_cast<float4 *>(qrow + VI * lane) = make_float4(out[0], out[1], out[2], out[3]);
-                    }
-                    __syncwarp();
-                    if (lane == 0) {
-                        mbar_arrive(&q_full[qs % RQ]);            // intermediate plane s: this row written
-                        mbar_arrive(&p_empty[(pc + s) % RP]);     // state plane m-1 is done
+                        __syncwarp();
+                        if (lane == 0) {
+                            mbar_arrive(&q_full[qs % RQ]);            // intermediate plane s: this row written
+                            mbar_arrive(&p_empty[(pc + s) % RP]);     // state plane m-1 is done
+                            mbar_arrive(&c_empty[(cc + s) % RC]);     // stage s is done
+                        }
                     }
 
-                    // ---- sweep 2 at plane m-1 from intermediate planes s-2 .. s
-                    if (s >= 2) {
+                    if (s >= 3) {
+                        // ---- sweep 2 at plane m-2 from intermediate planes s-3 .. s-1;
+                        // its coefficients come from global memory (the stage
+                        // that held them served sweep 1 two steps ago)
+                        const int m2 = m - 2;
+                        const size_t off = ((size_t)m2 * J + (size_t)j) * (size_t)pitch + (size_t)ib;
                         for (int qq = 0; qq < 3 && ok; ++qq) {
-                            const uint32_t qw = qc + s - 2 + qq;
+                            const uint32_t qw = qc + s - 3 + qq;
                             ok = mbar_wait_bounded(&q_full[qw % RQ], (qw / RQ) & 1);
                         }
                         ok = __all_sync(0xffffffffu, ok && !s_abort);
                         if (!ok) break;
                         if (do2) {
-                            const int m2 = m - 1;
                             const float *Qm =
-                                reinterpret_cast<const float *>(ring_q + (size_t)((qc + s - 2) % RQ) * S::Q_BYTES);
+                                reinterpret_cast<const float *>(ring_q + (size_t)((qs - 3) % RQ) * S::Q_BYTES);
                             const float *Qk =
-                                reinterpret_cast<const float *>(ring_q + (size_t)((qc + s - 1) % RQ) * S::Q_BYTES);
-                            const float *Qp = reinterpret_cast<const float *>(ring_q + (size_t)(qs % RQ) * S::Q_BYTES);
-                            const unsigned char *cs = ring_c + (size_t)((cc + s - 1) % RC) * S::C_BYTES;
+                                reinterpret_cast<const float *>(ring_q + (size_t)((qs - 2) % RQ) * S::Q_BYTES);
+                            const float *Qp =
+                                reinterpret_cast<const float *>(ring_q + (size_t)((qs - 1) % RQ) * S::Q_BYTES);
                             const int q0 = (w - 1) * TI, q1 = w * TI, q2r = (w + 1) * TI;
                             // columns i0-1 and i0+128 come from the edge warp
-                            const float(*Em)[2] = q_edge[(qc + s - 2) % RQ];
-                            const float(*Ek)[2] = q_edge[(qc + s - 1) % RQ];
-                            const float(*Ep)[2] = q_edge[qs % RQ];
+                            const float(*Em)[2] = q_edge[(qs - 3) % RQ];
+                            const float(*Ek)[2] = q_edge[(qs - 2) % RQ];
+                            const float(*Ep)[2] = q_edge[(qs - 1) % RQ];
                             float ek0[VI + 2], ek1[VI + 2], ek2[VI + 2], em1[VI + 2], ep1[VI + 2];
                             float vm0[VI], vm2[VI], vp0[VI], vp2[VI];
                             q_ext(Qk + q0, lane, Ek[w - 1][0], Ek[w - 1][1], ek0);
@@ -439,20 +469,22 @@ k_sweep2(const __grid_constant__ Sweep2Desc d, const Sweep2Args a)
                             lds_vec<float, VI>(Qm + q2r + VI * lane, vm2);
                             lds_vec<float, VI>(Qp + q0 + VI * lane, vp0);
                             lds_vec<float, VI>(Qp + q2r + VI * lane, vp2);
+                            // this lane's own copies (issued a step ago) have landed
+                            cp_async_wait_all();
                             float ca0[VI], ca1[VI], ca2[VI], ca3[VI], cb0[VI], cb1[VI], cb2[VI], cc0[VI], cc1[VI],
                                 cc2[VI], cwk[VI], cbn[VI];
-                            lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 0 * S::TILE) + cidx, ca0);
-                            lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 1 * S::TILE) + cidx, ca1);
-                            lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 2 * S::TILE) + cidx, ca2);
-                            lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 3 * S::TILE) + cidx, ca3);
-                            lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 4 * S::TILE) + cidx, cb0);
-                            lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 5 * S::TILE) + cidx, cb1);
-                            lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 6 * S::TILE) + cidx, cb2);
-                            lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 7 * S::TILE) + cidx, cc0);
-                            lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 8 * S::TILE) + cidx, cc1);
-                            lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 9 * S::TILE) + cidx, cc2);
-                            lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 10 * S::TILE) + cidx, cwk);
-                            lds_vec<float, VI>(reinterpret_cast<const float *>(cs + 11 * S::TILE) + cidx, cbn);
+                            lds_vec<float, VI>(buf2 + 0 * TI + VI * lane, ca0);
+                            lds_vec<float, VI>(buf2 + 1 * TI + VI * lane, ca1);
+                            lds_vec<float, VI>(buf2 + 2 * TI + VI * lane, ca2);
+                            lds_vec<float, VI>(buf2 + 3 * TI + VI * lane, ca3);
+                            lds_vec<float, VI>(buf2 + 4 * TI + VI * lane, cb0);
+                            lds_vec<float, VI>(buf2 + 5 * TI + VI * lane, cb1);
+                            lds_vec<float, VI>(buf2 + 6 * TI + VI * lane, cb2);
+                            lds_vec<float, VI>(buf2 + 7 * TI + VI * lane, cc0);
+                            lds_vec<float, VI>(buf2 + 8 * TI + VI * lane, cc1);
+                            lds_vec<float, VI>(buf2 + 9 * TI + VI * lane, cc2);
+                            lds_vec<float, VI>(buf2 + 10 * TI + VI * lane, cwk);
+                            lds_vec<float, VI>(buf2 + 11 * TI + VI * lane, cbn);
                             float out[VI];
                             float ss2 = 0.0f;
 #pragma unroll
@@ -464,12 +496,11 @@ k_sweep2(const __grid_constant__ Sweep2Desc d, const Sweep2Args a)
                                 const float ss = ss_f32_ec(c, ek1[e + 2], ek1[e], ek2[e + 1], ek0[e + 1], ep1[e + 1],
                                                            em1[e + 1], bij, bjk, bik, ca0[e], ca1[e], ca2[e], ca3[e],
                                                            cb0[e], cb1[e], cb2[e], cc0[e], cc1[e], cc2[e], cwk[e],
-                                                           cbn[e], ec_prev[e]);
+                                                           cbn[e], ec2[e]);
                                 out[e] = owned[e] ? fmaf(omega, ss, c) : c;
                                 if (res && owned[e]) ss2 = fmaf(ss, ss, ss2);
                             }
                             if (res) acc += (double)ss2;
-                            const size_t off = ((size_t)m2 * J + (size_t)j) * (size_t)pitch + (size_t)ib;
                             if (all_owned) {
                                 store_vec<float, VI>(p_out + off, out, st_pol);
                             } else {
@@ -479,22 +510,32 @@ k_sweep2(const __grid_constant__ Sweep2Desc d, const Sweep2Args a)
                             }
                         }
                         __syncwarp();
-                        if (lane == 0) mbar_arrive(&q_empty[(qc + s - 2) % RQ]);   // intermediate plane s-2 done
+                        if (lane == 0) mbar_arrive(&q_empty[(qs - 3) % RQ]);   // intermediate plane s-3 done
                     }
-                    if (s >= 1) {
+                    // the coefficients of the next step's sweep 2 (plane m-1),
+                    // into this warp's buffer, which sweep 2 above has read
+                    if (do2 && s + 1 >= 3 && s + 1 <= it.nout + 2) {   // the same for every lane
                         __syncwarp();
-                        if (lane == 0) mbar_arrive(&c_empty[(cc + s - 1) % RC]);  // stage s-1: both sweeps done
+                        if (any_owned) {
+                            const size_t offn = ((size_t)(m - 1) * J + (size_t)j) * (size_t)pitch + (size_t)ib;
+#pragma unroll
+                            for (int q = 0; q < 12; ++q)
+                                cp_async16(buf2 + q * TI + VI * lane, d.coef_ptr[q] + offn);
+                        }
+                        cp_async_commit();
                     }
 #pragma unroll
-                    for (int e = 0; e < VI; ++e) ec_prev[e] = ec_cur[e];
+                    for (int e = 0; e < VI; ++e) {
+                        ec2[e] = ec1[e];
+                        ec1[e] = ec0[e];
+                    }
                 }
                 if (!ok) break;
-                // the item's last state planes, stage and intermediate planes
+                // the item's last state planes and intermediate planes
                 __syncwarp();
                 if (lane == 0) {
                     mbar_arrive(&p_empty[(pc + it.nout + 2) % RP]);
                     mbar_arrive(&p_empty[(pc + it.nout + 3) % RP]);
-                    mbar_arrive(&c_empty[(cc + it.nout + 1) % RC]);
                     mbar_arrive(&q_empty[(qc + it.nout) % RQ]);
                     mbar_arrive(&q_empty[(qc + it.nout + 1) % RQ]);
                 }
@@ -531,6 +572,7 @@ k_sweep2(const __grid_constant__ Sweep2Desc d, const Sweep2Args a)
             s_abort = 1;
             atomicExch(&a.hdr->errword, (int)JAC_ETIMEOUT);
         }
+        cp_async_wait_all();   // no copy into this CTA's shared memory outlives it
     }
 
     // CTA epilogue: the last CTA to finish sums the partials in CTA order
