@@ -143,6 +143,57 @@ def variant_roofline(prec: str, gpts: float) -> dict:
     return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "peak_kind": kind}
 
 
+SWEEP2_FILES = ("jac_sweep2.cu", "jac_sweep_kernel.cuh", "jac_common.cuh")
+
+
+def sweep_split(w, prec, n, fuse=0):
+    """(two-sweep passes, single sweeps) of a call of n sweeps under the
+    library's plan for this grid (fuse 0: the library's choice): an even
+    number of passes when the resolved plan takes them and n >= 4."""
+    from paper_2002_12115_gb300.binding import resolve_plan
+    f = resolve_plan(w["I"], w["J"], w["K"], prec, fuse=fuse)["fuse"]
+    if prec != "f32" or f != 2 or n < 4:
+        return 0, n
+    n_pass = (n // 2) & ~1
+    return n_pass, n - 2 * n_pass
+
+
+def sweep_roofline(w, prec, n, ms, fuse=0) -> dict:
+    """Roofline of one call of n sweeps that took ms: HBM (FP32, BF16) or the
+    FP64 ALU for single sweeps; for two-sweep passes HBM at the pass's own
+    algorithmic bytes (every array read once and the state written once per
+    pass: 56 B per point per pass, 28 B per point-update), with the ceiling
+    that single sweeps' 56 B per point-update put on the same bandwidth."""
+    npts = n_interior(w)
+    gpts = npts * n / (ms * 1e-3) / 1e9
+    n_pass, rest = sweep_split(w, prec, n, fuse)
+    peak, kind = measured_peak()
+    key = f"{w['I']}x{w['J']}x{w['K']} {prec}"
+    if n_pass == 0:
+        r = variant_roofline(prec, gpts)
+        r.update({"kernel": "k_sweep", "algorithmic_bytes_per_launch": BYTES_PER_POINT[prec] * npts * n})
+        per_sweep = profiled_traffic(key)
+        traffic = per_sweep * n if per_sweep else None
+    else:
+        bytes_launch = BYTES_PER_POINT[prec] * npts * (n_pass + rest)
+        ach = bytes_launch / (ms * 1e-3) / 1e9
+        ceiling = peak / BYTES_PER_POINT[prec]
+        r = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "peak_kind": kind,
+             "kernel": "k_sweep2 (two sweeps per pass)" + (f" + {rest} single sweeps" if rest else ""),
+             "passes_per_launch": n_pass, "algorithmic_bytes_per_launch": bytes_launch,
+             "bytes_per_point_update": BYTES_PER_POINT[prec] / 2,
+             "single_sweep_ceiling": {"gpts": ceiling, "value_over_ceiling": gpts / ceiling,
+                                      "reading": "the rate single sweeps would reach at the full measured HBM "
+                                                 "bandwidth (56 B per point-update)"}}
+        per_pass = profiled_traffic(key + " two-sweep pass", SWEEP2_FILES)
+        traffic = per_pass * n_pass if (per_pass and rest == 0) else None
+    r["traffic"] = traffic
+    if traffic:
+        dram = traffic / (ms * 1e-3) / 1e9
+        r.update({"dram_achieved": dram, "dram_frac": dram / peak})
+    return r
+
+
 def kernel_source_hash(names=("jac_sweep_kernel.cuh", "jac_common.cuh")) -> str:
     h = hashlib.sha256()
     for name in names:
@@ -558,10 +609,13 @@ def bench_unhoisted(w, jac, host, sweeps=20):
     return n_interior(w) * sweeps / (time.perf_counter() - t0) / 1e9
 
 
-def bench_variant(w, prec, dev, stream, sweeps):
-    """Gpt/s of a precision on a grid (device-resident inputs)."""
+def bench_variant(w, prec, dev, stream, sweeps, fuse=0):
+    """Gpt/s of a precision on a grid (device-resident inputs); fuse as in
+    the launch plan (0: the library's choice)."""
     from paper_2002_12115_gb300 import Jacobi
     with Jacobi(w["I"], w["J"], w["K"], prec, 0.8, stream) as vj:
+        if fuse:
+            vj.set_plan(0, 0, 0, fuse)
         vj.upload_tensors(dev)
         vj.sweep(max(2, sweeps // 10)); vj.residual()
         a, b = events()
@@ -572,13 +626,8 @@ def bench_variant(w, prec, dev, stream, sweeps):
         ms = a.elapsed_time(b)
     gbs = BYTES_PER_POINT[prec] * n_interior(w) / (ms / sweeps * 1e-3) / 1e9
     gpts = n_interior(w) * sweeps / (ms * 1e-3) / 1e9
-    roofline = variant_roofline(prec, gpts)
-    per_sweep = profiled_traffic(f"{w['I']}x{w['J']}x{w['K']} {prec}")
-    if per_sweep:
-        dram = per_sweep / (ms / sweeps * 1e-3) / 1e9
-        roofline.update({"traffic_per_sweep": per_sweep, "dram_achieved": dram,
-                         "dram_frac": dram / measured_peak()[0]})
-    return {"value": gpts, "unit": UNIT, "ms_per_sweep": ms / sweeps,
+    roofline = sweep_roofline(w, prec, sweeps, ms, fuse)
+    return {"value": gpts, "unit": UNIT, "ms_per_sweep": ms / sweeps, "fuse": fuse,
             "gbs": gbs, "grid": [w["I"], w["J"], w["K"]], "prec": prec, "roofline": roofline}
 
 
@@ -1038,6 +1087,9 @@ def run_native(args, w, wname):
         for vp in ("bf16", "f64", "f32"):
             if vp != prec:
                 compare[vp] = bench_variant(w, vp, s["dev"], stream, min(n, 30 if vp == "f64" else 200))
+        if sweep_split(w, prec, n, args.fuse)[0]:
+            # the same grid in single sweeps: the DRAM-bound kernel the passes replace
+            compare[prec + "_single_sweeps"] = bench_variant(w, prec, s["dev"], stream, n, fuse=1)
         if prec != "f64":
             try:   # a reported comparison, not a timed figure: an error here is recorded, not raised
                 compare["residual_vs_f64_gpu"] = residual_vs_f64(w, s["dev"], stream, n)
@@ -1062,22 +1114,10 @@ def run_native(args, w, wname):
         compare["batched"] = bench_batch(args, stream, steps=2, autotune=not args.no_autotune)
         torch.cuda.empty_cache()
 
-    bytes_launch = BYTES_PER_POINT[prec] * n_interior(w) * n
-    achieved = bytes_launch / (s["launch_ms"] * 1e-3) / 1e9
-    per_sweep = profiled_traffic(f"{I}x{J}x{K} {prec}")
-    if prec == "f64":
-        roofline = variant_roofline("f64", n_interior(w) * n / (s["launch_ms"] * 1e-3) / 1e9)
-    else:
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "peak_kind": peak_kind}
-    roofline.update({"traffic": per_sweep * n if per_sweep else None, "kernel": "k_sweep",
-                     "algorithmic_bytes_per_launch": bytes_launch, "launch_ms": s["launch_ms"],
-                     "sweeps_per_launch": n})
-    if per_sweep:
-        # DRAM bandwidth actually drawn: the ncu bytes per sweep over the live
-        # launch time.  Below the algorithmic figure when arrays stay in L2.
-        dram = per_sweep * n / (s["launch_ms"] * 1e-3) / 1e9
-        roofline.update({"dram_achieved": dram, "dram_frac": dram / peak})
+    # dram_achieved: the ncu bytes of the launch over its live time (below
+    # the algorithmic figure when arrays stay in L2)
+    roofline = sweep_roofline(w, prec, n, s["launch_ms"], args.fuse)
+    roofline.update({"launch_ms": s["launch_ms"], "sweeps_per_launch": n})
     cpu = parity = None
     if want_oracle:
         fields = {k: v.numpy() for k, v in s["host"].items()}

@@ -139,11 +139,16 @@ typedef struct jac_plan {
     int tile_j;   /* rows per work item */
     int kdepth;   /* k-planes per work item, >= 1, or JAC_KDEPTH_BALANCED */
     int tile_i;   /* points per row */
-    int fuse;     /* two sweeps per pass (FP32 storage only): 0 the library's
-                     choice, which is single sweeps (on GB300 the two-sweep
-                     pass measured up to 26% slower: it halves the DRAM
-                     traffic but is bound by latency), 1 never, 2 whenever
-                     n_iter >= 4.  A pass reads the state once and writes it
+    int fuse;     /* two sweeps per pass (FP32 storage only; temporal
+                     blocking by two): 0 the library's choice, 1 never, 2
+                     whenever n_iter >= 4.  The library's choice (what
+                     jac_resolve_plan returns for 0) is 2 for FP32 grids
+                     whose two state buffers take more than half the L2
+                     (the device's, 128 MiB without one), where single sweeps
+                     are bound by DRAM bandwidth and a pass, which moves half
+                     the bytes per sweep, measured up to 1.26x faster on
+                     GB300; else 1 (a state that stays in L2 makes the single
+                     sweep faster).  A pass reads the state once and writes it
                      two sweeps later; the state is bitwise that of single
                      sweeps.  Its tile shape is fixed; tile_i, tile_j and
                      kdepth then apply to the 0..3 single sweeps that follow

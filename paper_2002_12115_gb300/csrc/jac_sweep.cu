@@ -295,6 +295,20 @@ int default_kdepth(long cols, int nk, int ctas, jac_prec prec)
 
 jac_plan resolve_plan(const jac_grid *g, const jac_plan *plan) { return resolve_plan_sms(g, plan, num_sms()); }
 
+// Whether the library's choice for a grid is two-sweep passes: FP32 storage
+// whose two state buffers do not stay in L2 (more than half of it; the L2
+// of the current device, or 128 MiB without one).  There the single sweep is
+// bound by DRAM bandwidth and a pass, which moves half the bytes per sweep,
+// is faster; where the state stays in L2 the single sweep is.
+bool two_sweep_default(const jac_grid *g)
+{
+    if (g->prec != JAC_F32) return false;
+    size_t l2 = device_l2_bytes();
+    if (l2 <= 1) l2 = (size_t)128 << 20;
+    const size_t state = 2 * (size_t)jac_pitch(g->I) * (size_t)g->J * (size_t)g->K * 4;
+    return state > l2 / 2;
+}
+
 // The plan of a grid for a device of `sms` SMs (one CTA per SM).
 jac_plan resolve_plan_sms(const jac_grid *g, const jac_plan *plan, int sms)
 {
@@ -304,6 +318,7 @@ jac_plan resolve_plan_sms(const jac_grid *g, const jac_plan *plan, int sms)
     int tj = 8;
     jac_plan p;
     p.fuse = plan ? plan->fuse : 0;
+    if (p.fuse == 0) p.fuse = two_sweep_default(g) ? 2 : 1;
     p.tile_i = (plan && plan->tile_i > 0) ? plan->tile_i : 0;
     p.tile_j = (plan && plan->tile_j > 0) ? plan->tile_j : 0;
     p.kdepth = (plan && (plan->kdepth > 0 || plan->kdepth == JAC_KDEPTH_BALANCED)) ? plan->kdepth : 0;

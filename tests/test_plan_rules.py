@@ -47,6 +47,24 @@ def test_explicit_entries_are_kept_and_the_rest_filled():
     assert plan(129, 129, 257, "f32", tile_j=16) == (64, 16, plan(129, 129, 257, "f32", tile_j=16)[2])
     assert plan(129, 129, 257, "f64", kdepth=KDEPTH_BALANCED)[2] == KDEPTH_BALANCED
     assert resolve_plan(129, 129, 257, "f32", sm_count=SMS, fuse=2)["fuse"] == 2
+    assert resolve_plan(513, 513, 1025, "f32", sm_count=SMS, fuse=1)["fuse"] == 1
+
+
+def test_two_sweep_passes_are_the_default_where_the_state_leaves_l2():
+    """fuse = 0 resolves to two-sweep passes for FP32 storage whose two state
+    buffers take more than half the L2 (128 MiB without a device), else to
+    single sweeps; BF16-coefficient and FP64 storage never take passes."""
+    def fuse(I, J, K, prec):
+        return resolve_plan(I, J, K, prec, sm_count=SMS)["fuse"]
+    assert fuse(513, 513, 1025, "f32") == 2          # 2.2 GB of state
+    assert fuse(257, 257, 513, "f32") == 2           # 278 MB
+    assert fuse(129, 129, 257, "f32") == 1           # 36 MB: stays in L2
+    assert fuse(33, 33, 65, "f32") == 1
+    # the boundary: 2 x pitch x J x K x 4 bytes against 64 MiB
+    assert fuse(128, 256, 256, "f32") == 1           # exactly 64 MiB
+    assert fuse(128, 256, 257, "f32") == 2           # 64.25 MiB
+    for prec in ("bf16", "f64"):
+        assert fuse(513, 513, 1025, prec) == 1
 
 
 @pytest.mark.parametrize("kw", [dict(tile_j=5), dict(tile_i=48), dict(tile_j=16, tile_i=128),
