@@ -672,6 +672,7 @@ jac_status jac_sweep_adjoint(jac_ctx *c, const double *lam_T, double *g_wrk1, do
         if (e != cudaSuccess) return ctx_cuda(c, e, "segment init");
     }
     jac_grid g = make_grid(c);
+    const bool pairs = c->prec == JAC_F32 && jac::resolve_plan(&g, &c->plan).fuse == 2;
     int lc = 0;
     const int nseg = (tp.taped + tp.C - 1) / tp.C;
     for (int sgi = nseg - 1; sgi >= 0; --sgi) {
@@ -679,10 +680,20 @@ jac_status jac_sweep_adjoint(jac_ctx *c, const double *lam_T, double *g_wrk1, do
         const int len = std::min(tp.C, tp.taped - t0);
         // state m of this segment: the checkpoint itself for m = 0
         auto state = [&](int m) -> void * { return m == 0 ? tp.ckpt(sgi) : tp.seg(m); };
-        for (int m = 1; m < len; ++m) {          // recompute the segment's states
+        // recompute the segment's states: where the plan takes two-sweep
+        // passes, one pass gives two states (the intermediate one stored on
+        // the way), bitwise those of single sweeps
+        for (int m = 1; m < len;) {
             g.p[0] = state(m - 1);
-            g.p[1] = tp.seg(m);
-            s = jac::sweep_dev(&g, &c->plan, 1, tp.scratch(), c->ws, c->ws_bytes, c->stream);
+            if (pairs && m + 1 < len) {
+                g.p[1] = tp.seg(m + 1);
+                s = jac::sweep2_run(&g, 0, 1, nullptr, c->ws, c->ws_bytes, c->stream, tp.seg(m));
+                m += 2;
+            } else {
+                g.p[1] = tp.seg(m);
+                s = jac::sweep_dev(&g, &c->plan, 1, tp.scratch(), c->ws, c->ws_bytes, c->stream);
+                m += 1;
+            }
             if (s != JAC_OK) return ctx_from_thread(c, s);
         }
         for (int m = len - 1; m >= 0; --m) {     // reverse sweeps of the segment

@@ -52,8 +52,13 @@ jac_status launch_sweep(jac_prec prec, int tj, const GridDesc &d0, const SweepAr
 // Two-sweep passes (FP32 storage): n_pass passes of two sweeps each, in one
 // cooperative launch; the residual of the last sweep to d_residual (NULL:
 // none).  kdepth 0: the default depth.
+// Two-sweep passes (FP32 storage): pass t reads p[t & 1] and writes the other
+// buffer.  mid (one-pass calls only) also receives the state after the first
+// sweep at every interior point; its faces are left as they are.
 jac_status sweep2_run(const jac_grid *g, int kdepth, int n_pass, double *d_residual, void *workspace,
-                      size_t ws_bytes, cudaStream_t st);
+                      size_t ws_bytes, cudaStream_t st, void *mid = nullptr);
+// Whether the library's plan for this grid takes two-sweep passes (fuse 0).
+bool two_sweep_default(const jac_grid *g);
 size_t sweep2_workspace_bytes(const jac_grid *g);
 jac_status adjoint_step_dev(const jac_grid *g, const void *p_t, const void *lam_in, void *lam_out, double *g_wrk1,
                             double *g_a3, double *const *g_coef, int kdepth, void *workspace, size_t ws_bytes,

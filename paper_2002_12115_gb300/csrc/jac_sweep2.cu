@@ -83,6 +83,7 @@ struct Sweep2Args {
     double omega;
     double *partials;          // gridDim.x
     double *res;               // residual of the last pass's second sweep (NULL: none)
+    float *mid;                // one-pass calls: also store sweep 1's state here (NULL: no)
     WsHeader *hdr;
     int l2_keep_state;
     unsigned l2_keep_coef;
@@ -426,6 +427,17 @@ k_sweep2(const __grid_constant__ Sweep2Desc d, const Sweep2Args a)
                         }
                         float *qrow = reinterpret_cast<float *>(ring_q + (size_t)(qs % RQ) * S::Q_BYTES) + w * TI;
                         *reinterpret_cast<float4 *>(qrow + VI * lane) = make_float4(out[0], out[1], out[2], out[3]);
+                        if (a.mid != nullptr && m >= it.kb && m < it.kb + it.nout) {
+                            // the intermediate state at this item's own points
+                            const size_t offm = ((size_t)m * J + (size_t)j) * (size_t)pitch + (size_t)ib;
+                            if (all_owned) {
+                                store_vec<float, VI>(a.mid + offm, out, st_pol);
+                            } else {
+#pragma unroll
+                                for (int e = 0; e < VI; ++e)
+                                    if (owned[e]) a.mid[offm + e] = out[e];
+                            }
+                        }
                         __syncwarp();
                         if (lane == 0) {
                             mbar_arrive(&q_full[qs % RQ]);            // intermediate plane s: this row written
@@ -658,9 +670,10 @@ size_t sweep2_workspace_bytes(const jac_grid *g)
 }
 
 jac_status sweep2_run(const jac_grid *g, int kdepth, int n_pass, double *d_residual, void *workspace,
-                      size_t ws_bytes, cudaStream_t st)
+                      size_t ws_bytes, cudaStream_t st, void *mid)
 {
     using S = Sweep2Shape;
+    if (mid != nullptr && n_pass != 1) return fail2(JAC_EINVAL, "the intermediate state needs a one-pass call");
     Sweep2Desc d;
     std::memset(&d, 0, sizeof(d));
     d.I = g->I; d.J = g->J; d.K = g->K;
@@ -696,6 +709,7 @@ jac_status sweep2_run(const jac_grid *g, int kdepth, int n_pass, double *d_resid
     a.omega = g->omega;
     a.partials = reinterpret_cast<double *>(static_cast<char *>(workspace) + kWsHeaderBytes);
     a.res = d_residual;
+    a.mid = static_cast<float *>(mid);
     a.hdr = hdr;
     SweepArgs la;
     std::memset(&la, 0, sizeof(la));
