@@ -58,3 +58,19 @@ def test_pairs_against_oracle():
     p, g = gpu_run(f, n, "f32", PAIRS)
     wp, wg = oracle_ref(f, n, "f32")
     assert rel_p(p, wp) <= TOL["f32"] and rel_g(g, wg) <= TOL["f32"], (rel_p(p, wp), rel_g(g, wg))
+
+
+def test_default_plan_takes_passes_where_the_state_leaves_l2():
+    """With no plan set, a grid whose two FP32 state buffers take more than
+    half the L2 runs two-sweep passes (the resolved plan says so) and gives
+    bitwise the state of single sweeps; a grid whose state stays in L2 keeps
+    single sweeps."""
+    from paper_2002_12115_gb300.binding import resolve_plan
+    assert resolve_plan(513, 513, 65, "f32")["fuse"] == 2
+    assert resolve_plan(129, 129, 257, "f32")["fuse"] == 1
+    I, J, K, n = 513, 513, 65, 6
+    f = ji.himeno_fields(I, J, K, seed=77)
+    p0, g0 = gpu_run(f, n, "f32")
+    p1, g1 = gpu_run(f, n, "f32", SINGLE)
+    assert np.array_equal(p0, p1), float(np.abs(p0 - p1).max())
+    assert abs(g0 - g1) <= 1e-9 * abs(g1), (g0, g1)
