@@ -194,11 +194,22 @@ def sweep_roofline(w, prec, n, ms, fuse=0) -> dict:
     return r
 
 
+def code_of(text: str) -> str:
+    """A CUDA/C++ source without its comments and with its whitespace
+    collapsed: what the compiler sees of it (the files have no string that
+    holds a comment marker)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_hash(names=("jac_sweep_kernel.cuh", "jac_common.cuh")) -> str:
+    """First 16 hex digits of the sha256 of the kernel sources' code (comments
+    and whitespace do not change it)."""
     h = hashlib.sha256()
     for name in names:
-        with open(os.path.join(ROOT, "paper_2002_12115_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2002_12115_gb300", "csrc", name)) as fh:
+            h.update(code_of(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -3,8 +3,10 @@
 // A pass reads the state p_t and writes p_{t+2}; the intermediate state
 // p_{t+1} of a tile lives only in shared memory.  Every coefficient plane is
 // then read from memory once for two point-updates.  Each update is the
-// same arithmetic as the single-sweep kernel (ss_f32), so a pass gives
-// bitwise the state of two single sweeps.
+// same arithmetic as the single-sweep kernel (ss_f32_ec; a3 S - 1, which
+// depends only on the coefficients, is formed by sweep 1 and carried in
+// registers to sweep 2 at the same point), so a pass gives bitwise the state
+// of two single sweeps.
 //
 // Kernel design (persistent, warp-specialised, one CTA per SM, all passes of
 // a call in one cooperative launch):
@@ -37,7 +39,10 @@
 //     columns belong to the neighbouring tiles, whose CTAs copy them at
 //     about the same time);
 //   * the residual of the last pass's second sweep is reduced as in the
-//     single-sweep kernel; every wait is bounded.
+//     single-sweep kernel; every wait is bounded;
+//   * a one-pass call may also store sweep 1's state at the points the
+//     items own (Sweep2Args::mid): the reverse pass recomputes two
+//     checkpoint-segment states per launch that way.
 //
 // Twelve warps leave 168 registers a thread (a thirteenth would put four
 // warps on one SM sub-partition and cap them at 128).
