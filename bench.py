@@ -184,7 +184,11 @@ def sweep_roofline(w, prec, n, ms, fuse=0) -> dict:
              "bytes_per_point_update": BYTES_PER_POINT[prec] / 2,
              "single_sweep_ceiling": {"gpts": ceiling, "value_over_ceiling": gpts / ceiling,
                                       "reading": "the rate single sweeps would reach at the full measured HBM "
-                                                 "bandwidth (56 B per point-update)"}}
+                                                 "bandwidth (56 B per point-update)"},
+             "reading": "a pass reads every array once per two point-updates; frac counts those bytes "
+                        "(28 B per point-update) against the copy peak, and the pass is bound by latency, "
+                        "not DRAM; the bandwidth fraction of single sweeps on the same grid (56 B per "
+                        "point-update) is compare." + prec + "_single_sweeps"}
         per_pass = profiled_traffic(key + " two-sweep pass", SWEEP2_FILES)
         traffic = per_pass * n_pass if (per_pass and rest == 0) else None
     r["traffic"] = traffic
